@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the linear Poisson-Boltzmann hot path on GB300.
+
+One step = one pass of the whole hot path for one synthetic molecule:
+grid placement + classification + crossing edges (pb_build_grid), edge
+weights + right-hand side (pb_assemble_coeffs), surface and pair Coulomb sums
+(pb_coulomb_terms), mixed-precision Jacobi-PCG to a true FP64 residual of
+1e-8 (pb_solve) and the energy terms (pb_energy).
+
+Default workload: 2,000-atom globular molecule (seed 2), uniform 257^3 grid
+spanning 1.5x the molecular extent, eps 2/80, 0.145 M salt, zero Dirichlet
+boundary.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own copy of
+the workload (independent problems, weak scaling, no data-path collective).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload (host cores only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s & DoF-iter/s (%HBM peak), p50/p99 latency vs plain FP64 CG at 1e-8 residual"
+WORKLOADS = {
+    "globular257": dict(n_atoms=2000, seed=2, n=257, fill=1.5, eps_in=2.0, eps_out=80.0,
+                        ionic=0.145, bc=0, rtol=1e-8),
+}
+# Stream (read+write) bytes per interior node of one launch of each FP32 PCG
+# kernel: direction kernel reads z, p_old (4 B each) and the code byte and
+# writes p; update kernel reads p, x, z and the code byte, writes x, z.
+ALG_BYTES_P32 = 4 * 3 + 1
+ALG_BYTES_U32 = 4 * 5 + 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="globular257", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.tmp.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+def oracle_sample(wl: dict, iters_needed: int | None, pcg_iters: int = 3,
+                  targets: int = 2000) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload and
+    extrapolate one full solve: full setup (classification, crossing edges,
+    coefficients, right-hand side) + `pcg_iters` PCG iterations scaled to
+    `iters_needed` + surface sums on `targets` flux points scaled to all of
+    them + the full pair sum."""
+    import numpy as np
+
+    import pb_inputs
+    from oracle import oracle as orc
+    orc.build()
+    atoms = pb_inputs.globular_molecule(wl["n_atoms"], seed=wl["seed"])
+    t0 = time.perf_counter()
+    g = orc.place_grid(atoms, wl["n"], wl["fill"])
+    lB, kD = orc.units(298.15, wl["ionic"], wl["eps_out"])
+    inside = orc.classify(g, atoms)
+    cross = orc.crossing_edges(g, atoms, inside)
+    coef = orc.assemble(g, inside, cross, wl["eps_in"], wl["eps_out"], kD)
+    phib = orc.bc_values(g, atoms, lB, wl["eps_out"], wl["bc"], kD)
+    f = orc.rhs(g, atoms, lB, coef, phib)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.pcg(g, coef, f, wl["rtol"], max_iter=pcg_iters)
+    t_iter = (time.perf_counter() - t0) / pcg_iters
+    flux = cross["sign"] != 0
+    nflux = int(flux.sum())
+    sel = np.flatnonzero(flux)[:: max(1, nflux // targets)][:targets]
+    t0 = time.perf_counter()
+    orc.coulomb_phi(cross["rp"][sel], atoms)
+    orc.coulomb_psi(cross["rp"][sel], (cross["ids"][sel] // g.N).astype(np.int8),
+                    cross["sign"][sel], atoms)
+    t_surf = (time.perf_counter() - t0) * nflux / len(sel)
+    t0 = time.perf_counter()
+    orc.ecoul(atoms, lB, wl["eps_in"])
+    t_pairs = time.perf_counter() - t0
+    iters = iters_needed or oracle_iters()
+    t_solve = t_setup + iters * t_iter + t_surf + t_pairs
+    return {"t_setup": t_setup, "t_iter": t_iter, "iters": iters, "t_surface": t_surf,
+            "t_pairs": t_pairs, "t_solve": t_solve, "nflux": nflux, "sampled_targets": len(sel),
+            "pcg_iters_sampled": pcg_iters}
+
+
+def oracle_iters() -> int:
+    """FP64 Jacobi-PCG iterations of the oracle to a 1e-8 true residual on
+    the default workload, as recorded by ``python -m oracle.calibrate`` (the
+    GPU FP64 path runs the same recurrence and reports its own count)."""
+    with open(os.path.join(ROOT, "oracle", "iters_globular257.json")) as fh:
+        return int(json.load(fh)["iters"])
+
+
+def cpu_baseline_obj(s: dict) -> dict:
+    return {"value": 1.0 / s["t_solve"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"full FP64 setup ({s['t_setup']:.1f} s), {s['pcg_iters_sampled']} PCG "
+                       f"iterations scaled to {s['iters']}, surface sums on "
+                       f"{s['sampled_targets']} of {s['nflux']} flux points scaled, full pair "
+                       f"sum; one host core, single-threaded C"),
+            "seconds_per_solve_est": s["t_solve"]}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(wl, None, pcg_iters=1, targets=200)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(wl, None))
+    wall = time.perf_counter() - t0
+    t_solve = statistics.mean(v["t_solve"] for v in vals)
+    value = 1.0 / t_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_solve, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_obj(args, wl),
+            "cpu_baseline": dict(cpu_baseline_obj(vals[-1]), value=value),
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+def config_obj(args, wl):
+    return {"workload": f"globular molecule {wl['n_atoms']} atoms, uniform {wl['n']}^3 grid, "
+                        f"fill {wl['fill']}, eps {wl['eps_in']:g}/{wl['eps_out']:g}, "
+                        f"{wl['ionic']} M, zero Dirichlet BC, rtol {wl['rtol']:g}",
+            "n_atoms": wl["n_atoms"], "grid": [wl["n"]] * 3, "seed": wl["seed"],
+            "parallelism": f"independent problems x{args.gpus}",
+            "l2": "inputs larger than L2 (working set ~1 GB per solve)"}
+
+
+# ------------------------------------------------------------------ ours --
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    import paper_2502_09323_gb300 as pb
+    import pb_inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2502_09323_gb300 import build
+    build.build()
+
+    atoms_np = pb_inputs.globular_molecule(wl["n_atoms"], seed=wl["seed"])
+    atoms_dev = torch.tensor(atoms_np, device=dev)
+    atoms_pin = torch.tensor(atoms_np).pin_memory()
+    spec = pb.GridSpec(n=(wl["n"],) * 3, fill=wl["fill"])
+    params = pb.Params(eps_in=wl["eps_in"], eps_out=wl["eps_out"], ionic_strength_M=wl["ionic"],
+                       bc=wl["bc"])
+
+    def step(atoms, precision):
+        g = pb.pb_build_grid(spec, atoms)
+        s = pb.pb_assemble_coeffs(g, params)
+        pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+        st = pb.pb_solve(s, pb.SolveOpts(precision=precision, rtol=wl["rtol"]))
+        e = pb.pb_energy(s)
+        return st, e, s
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        st, e, s = step(atoms_dev, pb.MIXED)
+        del s
+    # ---- timed region (device-resident inputs)
+    clocks = ClockSampler(dev.index)
+    barrier()
+    launches0 = pb.pb_kernel_launches()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    lat = []
+    stats = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st, e, s = step(atoms_dev, pb.MIXED)
+        lat.append(time.perf_counter() - t0)
+        stats.append(st)
+        last_sys = s
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = pb.pb_kernel_launches() - launches0
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    value = args.steps * world / elapsed
+    energy = e
+    dof = stats[-1]["dof"]
+    iters = statistics.mean(s_["iters_inner"] for s_ in stats)
+    solve_s = statistics.mean(s_["seconds"] for s_ in stats)
+
+    # ---- end to end through host buffers (pinned atoms in, energies out)
+    barrier()
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(args.steps):
+        st2, e2, s2 = step(atoms_pin, pb.MIXED)
+        del s2
+    ev3.record(stream)
+    barrier()
+    e2e_elapsed = max_over_ranks(ev2.elapsed_time(ev3) / 1e3)
+
+    # ---- plain FP64 Jacobi-PCG, same workload
+    fp64 = None
+    if not args.no_fp64:
+        step(atoms_dev, pb.FP64)
+        barrier()
+        ev4 = torch.cuda.Event(enable_timing=True)
+        ev5 = torch.cuda.Event(enable_timing=True)
+        k64 = max(1, min(2, args.steps))
+        ev4.record(stream)
+        st64 = []
+        for _ in range(k64):
+            st_, e64, s64 = step(atoms_dev, pb.FP64)
+            st64.append(st_)
+        ev5.record(stream)
+        barrier()
+        t64 = max_over_ranks(ev4.elapsed_time(ev5) / 1e3)
+        fp64 = {"solves_per_s": k64 * world / t64, "iters": st64[-1]["iters_inner"],
+                "true_rel_res": st64[-1]["true_rel_res"],
+                "dof_iter_per_s": st64[-1]["iters_inner"] * dof / st64[-1]["seconds"],
+                "e_total": e64["e_total"]}
+        fp64["speedup_mixed_over_fp64"] = value / fp64["solves_per_s"]
+
+    # ---- live kernel timing for the roofline (FP32 update kernel = dominant)
+    peak, peak_kind = load_peaks()
+    reps = 40
+    kt = {}
+    for which, name in ((1, "update"), (0, "direction")):
+        pb.pb_profile_kernels(last_sys, pb.MIXED, which, 3)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        pb.pb_profile_kernels(last_sys, pb.MIXED, which, reps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        kt[name] = a.elapsed_time(b) / 1e3 / reps
+    bytes_u = dof * ALG_BYTES_U32
+    achieved = bytes_u / kt["update"] / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stencil_update_fp32_globular257.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            traffic = json.load(fh).get("dram_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_stencil<float,CoefC32,MODE_U> (FP32 PCG update)",
+                "alg_bytes_per_launch": bytes_u, "launch_s": kt["update"],
+                "peak_kind": f"{peak_kind} hbm_gbs",
+                "direction_kernel": {"launch_s": kt["direction"],
+                                     "achieved_gbs": dof * ALG_BYTES_P32 / kt["direction"] / 1e9}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = oracle_sample(wl, fp64["iters"] if fp64 else None)
+        cpu = cpu_baseline_obj(smp)
+
+    lat_ms = sorted(1e3 * v for v in lat)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32 inner PCG + fp64 refinement", "data": "synthetic",
+        "config": config_obj(args, wl),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": args.steps * world / e2e_elapsed, "unit": "solves/s",
+                "h2d_bytes_per_step": int(atoms_np.nbytes), "d2h_bytes_per_step": 48},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "dof": dof, "iters_inner": iters, "iters_outer": stats[-1]["iters_outer"],
+        "true_rel_res": stats[-1]["true_rel_res"],
+        "dof_iter_per_s": iters * dof / solve_s, "solve_seconds": solve_s,
+        "latency_ms": {"p50": lat_ms[len(lat_ms) // 2],
+                       "p99": lat_ms[min(len(lat_ms) - 1, math.ceil(0.99 * len(lat_ms)) - 1)]},
+        "fp64_plain": fp64,
+        "energy_kT": energy,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,273 @@
+/*
+ * pb.h -- C ABI of the GB300 linear Poisson-Boltzmann hot path.
+ *
+ * The library solves the linearised Poisson-Boltzmann equation of
+ * NextGenPB (arXiv 2502.09323, Sec. 2.1, Eq. LPBE)
+ *
+ *     -div(eps grad phi) + eps_s k_D^2 chi_s phi = 4 pi l_B sum_i q_i delta(r - r_i)
+ *
+ * in reduced units (lengths in Angstrom, charges in e, phi in kT/e, energies
+ * in kT, permittivities relative, l_B the vacuum Bjerrum length at the given
+ * temperature) on the paper's box-method Cartesian grid (Sec. 3.1: primal-
+ * mixed Q1/Nedelec elements with vertex quadrature and static condensation),
+ * with the weighted-harmonic-average permittivity on surface-crossing edges
+ * (Sec. 3.2, Eq. WHA), and evaluates the energy partition of Eq. energyPart
+ * with the flux-based polarisation and ionic terms of Sec. 3.3.
+ *
+ * Discrete system, solved for the interior nodes:
+ *     (G^T W G + C) phi = f
+ *     W_e  = eps_e h on edge e, 1/eps_e = alpha_e/eps_in + (1-alpha_e)/eps_out,
+ *            alpha_e the fraction of the edge inside the solute;
+ *     C_kk = eps_out k_D^2 h^3 on solvent nodes, 0 on solute nodes;
+ *     f_k  = 4 pi l_B sum_i q_i w_k(r_i) (trilinear weights, Eq. RVop)
+ *            + W_e phi_b for every edge to a Dirichlet boundary node.
+ *
+ * Conventions of every array that crosses this boundary:
+ *   - node (i,j,k), 0 <= i < nx etc., has index (k*ny + j)*nx + i (x fastest)
+ *     and position origin + (i, j, k) * h;
+ *   - the edge from node a along axis d (0=x,1=y,2=z) has id d*N + a,
+ *     N = nx*ny*nz; it exists when that coordinate of a is < n_d - 1;
+ *   - the solute is the union of the atom balls; node a is inside when
+ *     |x_a - c|^2 < R^2 for some atom (a tie is solvent);
+ *   - atoms are rows (x, y, z, R, q), float64, row-major, n_atoms x 5.
+ *
+ * General rules:
+ *   - every function returns a pb_status and never aborts or exits;
+ *     pb_last_error() gives a message for the last failure of this thread;
+ *   - argument errors (NULL, NaN/Inf, negative radius, n < 3, a charge whose
+ *     trilinear cell touches the box boundary ...) return PB_ERR_ARG before
+ *     any work is queued;
+ *   - stream arguments are cudaStream_t values (NULL = legacy default stream);
+ *     all device work of a call is ordered on that stream;
+ *   - handles own all their device memory until pb_*_free; host arrays
+ *     passed in are read during the call only and never retained;
+ *   - device memory comes from the allocator installed with
+ *     pb_set_allocator, else from cudaMallocAsync on the call's stream;
+ *   - calls on distinct handles may run concurrently from different host
+ *     threads; a handle must not be used by two threads at once.
+ */
+#ifndef PB_H
+#define PB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PB_OK = 0,
+    PB_ERR_ARG = -1,     /* invalid argument; nothing was queued            */
+    PB_ERR_OOM = -2,     /* the allocator refused a request                 */
+    PB_ERR_CUDA = -3,    /* a CUDA call failed (message in pb_last_error)   */
+    PB_ERR_NOCONV = -4,  /* solver stopped without reaching the tolerance   */
+    PB_ERR_TIMEOUT = -5, /* the solve exceeded its time budget              */
+    PB_ERR_STATE = -6,   /* call out of order (e.g. pb_energy before solve) */
+    PB_ERR_UNIMPL = -7   /* feature not available in this build             */
+} pb_status;
+
+enum { PB_GRID_UNIFORM = 0, PB_GRID_OCTREE = 1 };
+enum { PB_BC_ZERO = 0, PB_BC_COULOMB = 1, PB_BC_DH = 2 };
+enum { PB_FP64 = 0, PB_MIXED = 1 };
+enum { PB_HOST = 0, PB_DEVICE = 1 };
+enum { PB_CT_BOUNDARY = 1, PB_CT_SURFACE = 2, PB_CT_PAIRS = 4, PB_CT_ALL = 7 };
+
+typedef struct pb_grid pb_grid;     /* opaque: geometry, inside flags, crossing list */
+typedef struct pb_system pb_system; /* opaque: coefficients, rhs, solution, energies  */
+
+/* Device-memory hooks.  alloc(ctx, bytes, stream) returns a device pointer
+ * (NULL on failure); release(ctx, ptr, stream) frees it.  Passing NULLs
+ * restores the default (cudaMallocAsync / cudaFreeAsync). */
+typedef void *(*pb_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*pb_free_fn)(void *ctx, void *ptr, void *stream);
+pb_status pb_set_allocator(pb_alloc_fn alloc, pb_free_fn release, void *ctx);
+
+/* Grid specification.  Uniform grid: n[3] nodes per axis (>= 3 each).
+ * If h > 0 the grid is origin + (i,j,k) h.  If h == 0 the grid is placed
+ * on the device (Sec. 2.3 "perfil", Sec. 3.4): a cube of side fill * extent
+ * (extent = largest axis span of the union of [x_i - R_i, x_i + R_i])
+ * centred on the atoms' bounding box, h = side / (max n - 1), n[0]==n[1]==n[2]
+ * required.  Octree fields are reserved (kind PB_GRID_OCTREE returns
+ * PB_ERR_UNIMPL). */
+typedef struct {
+    int32_t kind;
+    int32_t n[3];
+    double origin[3];
+    double h;
+    double fill;
+    double h_fine, h_bulk, refine_dist;
+} pb_grid_spec;
+
+/* Physical parameters (Sec. 2.1, 2.3).  eps_in/eps_out relative
+ * permittivities of solute/solvent; 1:1 salt of ionic strength I (mol/L);
+ * temperature in K; bc one of PB_BC_*:
+ *   ZERO     phi_b = 0 (homogeneous Dirichlet);
+ *   COULOMB  phi_b = (l_B/eps_out) sum_i q_i / r;
+ *   DH       phi_b = (l_B/eps_out) sum_i q_i exp(-k_D r) / r. */
+typedef struct {
+    double eps_in, eps_out, ionic_strength_M, temperature_K;
+    int32_t bc;
+} pb_params;
+
+/* Solver options.  precision PB_FP64: Jacobi-PCG entirely in FP64.
+ * PB_MIXED: FP64 iterative refinement around an FP32 Jacobi-PCG (FP32
+ * stencil, vectors and per-thread accumulation, FP64 global dots).
+ * Stop when ||f - A phi||_2 <= rtol ||f||_2 (true residual, FP64).
+ * max_iter caps the total inner iterations, max_outer the refinement
+ * steps; inner_rtol (0 = default 1e-4) is the inner relative tolerance;
+ * time_budget_s (0 = none) bounds the wall time of the call. */
+typedef struct {
+    int32_t precision;
+    double rtol;
+    int32_t max_iter, max_outer;
+    double inner_rtol, time_budget_s;
+} pb_solve_opts;
+
+typedef struct {
+    int32_t status;           /* pb_status of the solve                     */
+    int32_t iters_inner;      /* PCG iterations (FP32 inner or FP64 plain)  */
+    int32_t iters_outer;      /* FP64 residual evaluations                  */
+    double true_rel_res;      /* ||f - A phi|| / ||f|| in FP64 at exit      */
+    double seconds;           /* host wall time of the call                 */
+    int64_t dof;              /* interior unknowns                          */
+    int64_t model_bytes;      /* modelled DRAM bytes of the solve           */
+} pb_solve_stats;
+
+/* Energy terms in kT (Sec. 3.3, Eq. energyPart):
+ *   e_coul      (l_B/eps_in) sum_{i<j} q_i q_j / r_ij;
+ *   e_pol       1/2 (1/eps_out - 1/eps_in) sum_e F_e Phi_e / (4 pi);
+ *   e_ion_flux  -1/2 (1/eps_out) sum_e F_e Phi_e / (4 pi)  (second integral
+ *               of Eq. energy_ion);
+ *   e_ion_surf  1/2 sum_e phi(r_e) h^2 Psi_e / (4 pi)  (first integral of
+ *               Eq. energy_ion on the staircase dual faces of the flux edges,
+ *               phi(r_e) from Eq. phi0) -- a stand-in for the paper's
+ *               triangulated surface;
+ *   e_total     sum of the four;
+ *   flux_charge sum_e F_e / (4 pi l_B): the enclosed charge by Gauss' law.
+ * F_e = W_e (phi_in - phi_out) over flux edges (endpoints in different
+ * media), Phi_e = sum_i q_i/|r_e - r_i|, Psi_e = sum_i q_i (r_e - r_i).n_e /
+ * |r_e - r_i|^3, n_e the unit edge direction from the inside endpoint. */
+typedef struct {
+    double e_coul, e_pol, e_ion_surf, e_ion_flux, e_total, flux_charge;
+} pb_energy_terms;
+
+typedef struct {
+    int32_t n[3];
+    double origin[3];
+    double h;
+    int64_t n_nodes;          /* nx*ny*nz                                  */
+    int64_t n_atoms;
+    int64_t n_cross;          /* listed edges (see PB_ARR_CROSS_ID)        */
+    int64_t n_flux;           /* listed edges whose endpoints differ       */
+    int64_t n_inside;         /* solute nodes                              */
+} pb_grid_info;
+
+/* Arrays that pb_get_array copies out (element type, length). */
+enum {
+    PB_ARR_INSIDE = 0,   /* uint8  [N]      1 = solute node                     */
+    PB_ARR_CROSS_ID,     /* int64  [n_cross] ids of listed edges, increasing:
+                            edges with 0 < alpha < 1 or with endpoints in
+                            different media                                   */
+    PB_ARR_CROSS_ALPHA,  /* double [n_cross] inside fraction alpha             */
+    PB_ARR_CROSS_RP,     /* double [3*n_cross] r_e: alpha*h from the inside
+                            endpoint towards the outside one (Sec. 3.3.1);
+                            edge midpoint when both endpoints share a medium  */
+    PB_ARR_CROSS_SIGN,   /* int8   [n_cross] +1 / -1: inside endpoint is the
+                            low / high node; 0 same medium                    */
+    PB_ARR_WX,           /* double [N] W of edge (a -> a+x), 0 if none       */
+    PB_ARR_WY,           /* double [N]                                       */
+    PB_ARR_WZ,           /* double [N]                                       */
+    PB_ARR_KAPPA,        /* double [N] C_kk = eps_out k_D^2 h^3 or 0           */
+    PB_ARR_DIAG,         /* double [N] diagonal of A (0 on boundary nodes)   */
+    PB_ARR_RHS,          /* double [N] f, 0 on boundary nodes                */
+    PB_ARR_BC,           /* double [N] phi_b on boundary nodes, 0 inside     */
+    PB_ARR_PHI,          /* double [N] solution incl. boundary values        */
+    PB_ARR_PHI_SURF,     /* double [n_cross] Phi_e (0 on non-flux edges)     */
+    PB_ARR_PSI_SURF,     /* double [n_cross] Psi_e (0 on non-flux edges)     */
+    PB_ARR_COUNT
+};
+
+/* pb_build_grid -- grid placement, node classification and the list of
+ * surface-crossing edges (Sec. 2.1 eps(r); Sec. 3.2 alpha and the crossing
+ * points of Eq. WHA; Sec. 2.3 perfil).  atoms: n_atoms x 5 doubles at
+ * atoms_loc (PB_HOST or PB_DEVICE).  On success *out owns a new grid.  The
+ * call synchronises the stream once (to size the crossing list). */
+pb_status pb_build_grid(const pb_grid_spec *spec, const double *atoms, int64_t n_atoms,
+                        int32_t atoms_loc, void *stream, pb_grid **out);
+pb_status pb_grid_info_get(const pb_grid *g, pb_grid_info *info);
+void pb_grid_free(pb_grid *g);
+
+/* pb_assemble_coeffs -- edge weights W (Sec. 3.1 vertex quadrature +
+ * Sec. 3.2 WHA), the ionic diagonal C (Sec. 2.1 linearisation), boundary
+ * values (Sec. 2.3) and the right-hand side (Eq. RVop + Dirichlet lift).
+ * The Coulomb/DH boundary values are an N-body sum over the box faces run
+ * by this call.  The system keeps a reference to g (g must outlive it). */
+pb_status pb_assemble_coeffs(pb_grid *g, const pb_params *params, void *stream,
+                             pb_system **out);
+void pb_system_free(pb_system *s);
+
+/* pb_coulomb_terms -- analytic N-body sums of Sec. 3.3: PB_CT_SURFACE
+ * computes Phi_e and Psi_e at the crossing points of flux edges; PB_CT_PAIRS
+ * the Coulomb energy; PB_CT_BOUNDARY recomputes the boundary values.  FP32
+ * tiled kernel with split (hi+lo) coordinates and compensated sums, FP64
+ * results, kept on the device inside s. */
+pb_status pb_coulomb_terms(pb_system *s, int32_t which, void *stream);
+
+/* pb_solve -- Jacobi-preconditioned CG for (G^T W G + C) phi = f (the
+ * Krylov solve of Eq. matrixequation), zero initial guess, in the
+ * precision of opts.  On PB_OK or PB_ERR_NOCONV the best phi is kept in s.
+ * If phi_dev is not NULL the solution (all N nodes, boundary values
+ * included, double) is also copied to that device buffer. */
+pb_status pb_solve(pb_system *s, const pb_solve_opts *opts, double *phi_dev, void *stream,
+                   pb_solve_stats *stats);
+
+/* pb_energy -- energy terms of Sec. 3.3 from the solved phi; needs
+ * pb_solve and pb_coulomb_terms(PB_CT_SURFACE|PB_CT_PAIRS) first
+ * (PB_ERR_STATE otherwise).  *out is written on the host (the call
+ * synchronises the stream). */
+pb_status pb_energy(pb_system *s, void *stream, pb_energy_terms *out);
+
+/* pb_get_phi -- copy the solution (N doubles) to dst (PB_HOST/PB_DEVICE). */
+pb_status pb_get_phi(pb_system *s, double *dst, int32_t dst_loc, void *stream);
+
+/* pb_get_array -- copy one of the PB_ARR_* arrays to dst (host or device);
+ * grid arrays (INSIDE, CROSS_*) may be read with s == NULL and g set.
+ * bytes must be at least the array size. */
+pb_status pb_get_array(const pb_grid *g, const pb_system *s, int32_t which, void *dst,
+                       size_t bytes, int32_t dst_loc, void *stream);
+
+/* pb_apply -- y = A x on interior nodes (boundary entries of x are read as
+ * zero, y is zero on boundary nodes); x, y are device arrays of N elements
+ * in node order: double for PB_FP64, float for PB_MIXED (the FP32 operator
+ * used by the inner solver). */
+pb_status pb_apply(pb_system *s, int32_t precision, const void *x, void *y, void *stream);
+
+/* pb_solve_batch -- solve n independent systems (different molecules and
+ * grid sizes) with one persistent, CUDA-graph-launched mixed-precision
+ * solver; stats has n entries.  All systems must live on the same device. */
+pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_opts *opts,
+                         void *stream, pb_solve_stats *stats);
+
+/* pb_profile_kernels -- timing hook: run `reps` launches of the PCG kernels
+ * of the given precision on s's solver state with the convergence test off
+ * (iterate and state are overwritten, so call it after pb_energy).  which:
+ * 0 = direction kernel (p = z + beta p, A p, p.Ap), 1 = update kernel (A p,
+ * x and z update, the two dots), 2 = both (one PCG iteration per rep).
+ * Needs a prior pb_solve in that precision (PB_ERR_STATE otherwise). */
+pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int32_t reps,
+                             void *stream);
+
+/* Number of CUDA kernels launched by this library in this process so far. */
+int64_t pb_kernel_launches(void);
+
+/* Thread-local message describing the last failure ("" if none). */
+const char *pb_last_error(void);
+/* Library version string. */
+const char *pb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PB_H */

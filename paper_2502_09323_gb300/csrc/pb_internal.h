@@ -1,0 +1,199 @@
+// Internal declarations shared by the CUDA translation units of libpbgpu.
+// Nothing here is part of the public C ABI (include/pb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pb.h"
+
+namespace pbg {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char *fmt, ...);
+void note_launch(long long n);
+#define PB_CUDA_TRY(expr)                                                         \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            ::pbg::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                             __FILE__, __LINE__);                                 \
+            return PB_ERR_CUDA;                                                   \
+        }                                                                         \
+    } while (0)
+#define PB_LAUNCH_CHECK()          \
+    do {                           \
+        ::pbg::note_launch(1);     \
+        PB_CUDA_TRY(cudaGetLastError()); \
+    } while (0)
+
+// ------------------------------------------------------------- allocator --
+void *dalloc(size_t bytes, cudaStream_t s);   // nullptr on failure
+void dfree(void *p, cudaStream_t s);
+
+// Device-side error flags written by kernels (bit mask).
+enum : uint32_t {
+    ERRF_ATOM_VALUE = 1u,      // NaN/Inf coordinate or non-positive radius
+    ERRF_CHARGE_CELL = 2u,     // a charge's trilinear cell touches the boundary
+    ERRF_TOO_MANY_BALLS = 4u,  // more than MAX_EDGE_BALLS balls meet one edge
+    ERRF_CELL_OVERFLOW = 8u,   // atom cell list inconsistent
+};
+constexpr int MAX_EDGE_BALLS = 48;
+
+// Geometry and build summary computed on the device and read back once.
+struct BuildInfo {
+    double lo[3], hi[3];  // bounding box of the atom balls
+    double origin[3], h;  // grid placement
+    double rmax;          // largest radius
+    uint32_t err;         // ERRF_* bits
+    uint32_t pad;
+    unsigned long long ncross, nflux, ninside;
+};
+
+// Atom cell list used by the crossing-edge pass and the charge deposit.
+struct CellList {
+    double lo[3];     // corner of cell (0,0,0)
+    double cs;        // cell side
+    int dim[3];
+    int ncell;
+    int *start;       // [ncell + 1]
+    int *atom;        // [na] atom ids grouped by cell
+};
+
+// Grid geometry passed by value to kernels.
+struct GridGeo {
+    int nx, ny, nz;
+    long long N;          // nx*ny*nz (canonical node count)
+    double o[3];
+    double h;
+};
+
+// Padded FP32/FP64 solver layout: rows padded to a multiple of 4 elements.
+struct PadGeo {
+    int nx, ny, nz;
+    int sx;               // padded row length
+    long long sxy;        // sx * ny
+    long long Np;         // sx * ny * nz
+    long long N;          // canonical nx*ny*nz
+};
+
+}  // namespace pbg
+
+struct pb_grid {
+    int device;
+    cudaStream_t stream;  // creation stream; memory is released on it
+    pbg::GridGeo geo;
+    long long na;
+    double *atoms;        // SoA: x[na], y[na], z[na], R[na], q[na]
+    uint8_t *inside;      // [N] 1 = solute
+    uint8_t *near_;       // [N] 1 = within R + h of some atom centre
+    pbg::CellList cells;
+    long long ncross, nflux, ninside;
+    long long *cid;       // [ncross] edge ids, increasing
+    double *calpha;       // [ncross]
+    double *crp;          // [3*ncross] AoS
+    int8_t *csign;        // [ncross]
+    int *rowstart;        // [3*ny*nz + 1] first list entry of each edge row
+    pbg::BuildInfo *d_info;
+    double center[3];     // shift used by the FP32 N-body kernels
+};
+
+namespace pbg {
+
+// Device scalars of one PCG solve.
+struct CgState {
+    double rho;      // r.z of the current iterate
+    double alpha, beta;
+    double rr;       // ||r||^2 of the current iterate
+    double rr_stop;  // stop when rr <= rr_stop
+    double rr0;
+    double sigma;
+    double res64;    // ||f - A phi||^2 from the FP64 residual pass
+    double rz64;     // r.(r/diag) from the FP64 residual pass
+    int iter;        // iterations done
+    int max_iter;
+    int done;        // 1 = converged or stopped
+    int status;      // 0 ok, 1 breakdown, 2 max_iter
+    unsigned int counter;  // last-block counter of the reductions
+    int profile;     // 1 = timing run: never stop
+};
+
+struct EnergyAcc {
+    double S, I, F;  // sum F*Phi, sum phi(rp) h^2 Psi, sum F
+    double ecoul_sum;
+    pb_energy_terms out;
+    unsigned int counter;
+    unsigned int pad;
+};
+
+}  // namespace pbg
+
+struct pb_system {
+    pb_grid *g;
+    cudaStream_t stream;
+    pb_params p;
+    double lB, kD, kap_s;
+    double *W[3];       // canonical FP64 edge weights
+    double *diag;       // canonical FP64 diagonal (0 on boundary)
+    double *rhs;        // canonical f
+    double *bc;         // canonical boundary values (0 inside)
+    double *phi;        // canonical solution incl. boundary values
+    pbg::PadGeo pad;
+    uint8_t *code;      // padded: bit0 solute, bit1..3 +x/+y/+z edge listed
+    float *w32[3];      // padded FP32 edge weights (read only where listed)
+    // FP32 mixed solver workspace (padded layout)
+    float *z32, *pa32, *pb32, *d32;
+    // FP64 plain solver workspace (padded layout)
+    double *z64, *pa64, *pb64, *x64;
+    double *partials;   // reduction partials
+    int npartials;
+    pbg::CgState *st;
+    pbg::CgState *h_st; // pinned host mirror
+    double *Phi, *Psi;  // [ncross]
+    double *ecoul_phi;  // [na] Phi at atoms (self excluded)
+    pbg::EnergyAcc *eacc;
+    pb_energy_terms *h_energy;  // pinned
+    int solved, have_surface, have_pairs;
+    double fnorm2;
+};
+
+namespace pbg {
+
+// ---------------------------------------------------------------- grid.cu --
+pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s);
+
+// ----------------------------------------------------------- assemble.cu --
+pb_status assemble(pb_system *sys, cudaStream_t s);
+pb_status deposit_rhs(pb_system *sys, cudaStream_t s);
+pb_status fill_kappa(const pb_system *sys, double *dst, cudaStream_t s);
+
+// -------------------------------------------------------------- nbody.cu --
+pb_status nbody_boundary(pb_system *sys, cudaStream_t s);
+pb_status nbody_surface(pb_system *sys, cudaStream_t s);
+pb_status nbody_pairs(pb_system *sys, cudaStream_t s);
+
+// -------------------------------------------------------------- solve.cu --
+pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve_stats *st);
+pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaStream_t s);
+pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s);
+pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cudaStream_t s);
+
+// ------------------------------------------------------------- energy.cu --
+pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);
+
+// helpers
+inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+inline int num_sms() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 1;
+    }
+    return v;
+}
+
+}  // namespace pbg

@@ -1,0 +1,1004 @@
+// Krylov solve of the condensed system A phi = f (Sec. 3.1, Eq.
+// matrixequation): Jacobi-preconditioned conjugate gradient with fused
+// stencil/dot/axpy kernels, in FP64, or in FP32 inside FP64 iterative
+// refinement.
+//
+// Iteration (z = D^-1 r is stored instead of r; r = D z is formed on the fly):
+//   kernel P:  p <- z + beta p ;  q = A p ;  sigma = p.q      -> alpha = rho/sigma
+//   kernel U:  q = A p (recomputed) ; x += alpha p ; z -= alpha D^-1 q ;
+//              rho' = (Dz).z ; rr = |Dz|^2                    -> beta = rho'/rho
+// Each kernel marches a tile of 32*VEC x TY nodes along z, keeping the p
+// values of three planes in registers and one plane (plus the y halo rows,
+// computed by two extra warps) in shared memory; x neighbours come from warp
+// shuffles and one extra load at each tile edge.  Every global vector access
+// is a 16-byte vector access on rows padded to a multiple of 4 elements.
+// Dot products are accumulated per thread in the working precision and
+// reduced across the grid in FP64 with a fixed order (last-block pattern),
+// so results are deterministic.
+//
+// FP32 operator: per node one code byte (bit 0 solute, bits 1..3 "the +x/+y/+z
+// edge is listed"); unlisted edges have the pure weight eps h of the node's
+// medium, listed edges read their FP32 weight from the crossing list, found by
+// a binary search inside the edge's row.  The diagonal is rebuilt from the
+// six weights and the node's ionic term, so no coefficient array is streamed.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "pb_internal.h"
+
+namespace pbg {
+
+namespace {
+
+template <typename T>
+struct VT;
+template <>
+struct VT<float> {
+    using V = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct VT<double> {
+    using V = double2;
+    static constexpr int N = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void vload(const T *p, T (&v)[VT<T>::N]);
+template <>
+__device__ __forceinline__ void vload<float>(const float *p, float (&v)[4]) {
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void vload<double>(const double *p, double (&v)[2]) {
+    double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T *p, const T (&v)[VT<T>::N]);
+template <>
+__device__ __forceinline__ void vstore<float>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void vstore<double>(double *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+
+template <int VEC>
+__device__ __forceinline__ uint32_t cload(const uint8_t *p);
+template <>
+__device__ __forceinline__ uint32_t cload<4>(const uint8_t *p) {
+    return *reinterpret_cast<const uint32_t *>(p);
+}
+template <>
+__device__ __forceinline__ uint32_t cload<2>(const uint8_t *p) {
+    return (uint32_t) * reinterpret_cast<const uint16_t *>(p);
+}
+__device__ __forceinline__ uint8_t cbyte(uint32_t c, int v) { return (uint8_t)(c >> (8 * v)); }
+
+// ------------------------------------------------------ operator providers --
+// Compressed FP32 operator: weights of unlisted edges are the pure medium
+// value of the node's code byte; a listed edge reads its FP32 weight from
+// the padded per-node arrays wx/wy/wz, which are touched only for listed
+// edges (a few percent of faces), so they are not streamed.
+struct CoefC32 {
+    static constexpr bool kCompressed = true;
+    const float *wx, *wy, *wz;
+    float w_in, w_out, kap;
+    // weight of the edge along d whose low node has padded index pl and
+    // code cl; cs is the code of the node being updated
+    __device__ __forceinline__ float w(int d, int, int, int, int pl, uint8_t cl, uint8_t cs) const {
+        const float *W = d == 0 ? wx : (d == 1 ? wy : wz);
+        return ((cl >> (1 + d)) & 1) ? __ldg(W + pl) : ((cs & 1) ? w_in : w_out);
+    }
+    __device__ __forceinline__ float pure(uint8_t cs) const { return (cs & 1) ? w_in : w_out; }
+    __device__ __forceinline__ float kappa(uint8_t cs) const { return (cs & 1) ? 0.f : kap; }
+};
+
+// Stored FP64 weights (canonical layout): the plain FP64 solver and the
+// FP64 apply stream the three weight arrays.
+struct CoefS64 {
+    static constexpr bool kCompressed = false;
+    const double *W0, *W1, *W2;
+    double kap;
+    int nx, ny;
+    __device__ __forceinline__ double w(int d, int i, int j, int k, int, uint8_t, uint8_t) const {
+        int a = (k * ny + j) * nx + i;
+        return d == 0 ? W0[a] : (d == 1 ? W1[a] : W2[a]);
+    }
+    __device__ __forceinline__ double pure(uint8_t) const { return 0.0; }
+    __device__ __forceinline__ double kappa(uint8_t cs) const { return (cs & 1) ? 0.0 : kap; }
+};
+
+enum { MODE_P = 0, MODE_U = 1, MODE_A = 2 };
+
+template <typename T>
+struct KArgs {
+    const T *in;     // P: z ; U: p ; A: x
+    const T *in2;    // P: p_old
+    T *out;          // P: p_new ; A: y
+    T *xv;           // U: x (solution increment)
+    T *zv;           // U: z
+    const uint8_t *code;
+    CgState *st;
+    double *partials;
+    PadGeo pg;
+    int KC;
+};
+
+// block-wide FP64 sum of v (valid in thread 0)
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sred) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sred[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NT / 32; ++q) t += sred[q];
+    __syncthreads();
+    return t;
+}
+
+// Sum partials[0..nb) (and partials[nb..2nb) when TWO) in a fixed order by the
+// last block to finish; returns true in that block (all threads).
+template <int NT, bool TWO>
+__device__ bool last_block_total(CgState *st, double *partials, int nb, double mine0,
+                                 double mine1, double *sred, double &tot0, double &tot1) {
+    __shared__ int s_last;
+    int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double b0 = block_sum<NT>(mine0, sred);
+    double b1 = TWO ? block_sum<NT>(mine1, sred) : 0.0;
+    if (threadIdx.x == 0) {
+        partials[bid] = b0;
+        if (TWO) partials[nb + bid] = b1;
+        __threadfence();
+        unsigned t = atomicAdd(&st->counter, 1u);
+        s_last = (t == (unsigned)nb - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = threadIdx.x; q < nb; q += NT) {
+        a0 += __ldcg(partials + q);
+        if (TWO) a1 += __ldcg(partials + nb + q);
+    }
+    tot0 = block_sum<NT>(a0, sred);
+    tot1 = TWO ? block_sum<NT>(a1, sred) : 0.0;
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void sstore(T *dst, const T (&v)[VT<T>::N]) {
+    vstore<T>(dst, v);
+}
+
+// code bytes of a lane's VEC points packed in one word
+template <int VEC>
+struct CodeW;
+template <>
+struct CodeW<4> {
+    using W = uint32_t;
+    static constexpr uint32_t rep(uint32_t b) { return b * 0x01010101u; }
+};
+template <>
+struct CodeW<2> {
+    using W = uint32_t;
+    static constexpr uint32_t rep(uint32_t b) { return b * 0x0101u; }
+};
+
+// One stencil kernel for the three uses (MODE_P / MODE_U / MODE_A).
+// Each warp owns one grid row j (32*VEC consecutive x nodes, VEC per lane)
+// and marches along z over KC planes, carrying its row of planes k-1, k, k+1
+// in registers; the rows j-1 and j+1 of plane k are read from L1/L2 (the
+// neighbouring warps streamed them from HBM moments earlier), x neighbours
+// come from warp shuffles plus one scalar load at each tile edge.  Warps
+// never wait on each other; a block only synchronises for its final
+// reduction.
+template <typename T, class CP, int MODE, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB)
+k_stencil(KArgs<T> A, CP cp) {
+    constexpr int VEC = VT<T>::N;
+    constexpr int NT = 32 * WARPS;
+    constexpr int TXP = 32 * VEC;
+    __shared__ double sred[NT / 32];
+
+    T alpha = 0, beta = 0;
+    if (MODE != MODE_A) {
+        if (A.st->done) return;
+        if (MODE == MODE_P) beta = (T)A.st->beta;
+        if (MODE == MODE_U) alpha = (T)A.st->alpha;
+    }
+    const PadGeo g = A.pg;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * TXP;
+    const int ib = i0 + lane * VEC;  // first point of this lane
+    const int j = 1 + blockIdx.y * WARPS + w;
+    const int k0 = 1 + blockIdx.z * A.KC;
+    const int k1 = min(k0 + A.KC, g.nz - 1);
+    const bool active = j <= g.ny - 2;
+    const bool grp_ok = active && ib < g.sx;
+    const bool hl = active && lane == 0 && i0 > 0;
+    const bool hr = active && lane == 31 && i0 + TXP < g.sx;
+    const int sx = g.sx, sxy = (int)g.sxy;
+
+    // streamed value at padded index q0 (P mode forms z + beta p_old)
+    auto ldv = [&](int q0, T (&v)[VEC]) {
+        vload<T>(A.in + q0, v);
+        if (MODE == MODE_P) {
+            T po[VEC];
+            vload<T>(A.in2 + q0, po);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) v[q] = v[q] + beta * po[q];
+        }
+    };
+    auto lds = [&](int q0) -> T {
+        T v = A.in[q0];
+        if (MODE == MODE_P) v = v + beta * A.in2[q0];
+        return v;
+    };
+
+    T pm[VEC], pc[VEC], pn[VEC];
+    uint32_t cm = 0, cc = 0, cn = 0;
+    T lc = 0, rc = 0, ln = 0, rn = 0;
+    uint32_t lcc = 0, lcn = 0;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) pm[q] = pc[q] = pn[q] = 0;
+    if (grp_ok) {
+        const int b0 = (k0 - 1) * sxy + j * sx + ib;
+        ldv(b0, pm);
+        cm = cload<VEC>(A.code + b0);
+        ldv(b0 + sxy, pc);
+        cc = cload<VEC>(A.code + b0 + sxy);
+    }
+    if (hl) {
+        const int q0 = k0 * sxy + j * sx + i0 - 1;
+        lc = lds(q0);
+        lcc = A.code[q0];
+    }
+    if (hr) rc = lds(k0 * sxy + j * sx + i0 + TXP);
+
+    // fast-path diagonals of the two pure media and their inverses
+    T dg_in = 1, dg_out = 1, dinv_in = 1, dinv_out = 1;
+    if (CP::kCompressed) {
+        dg_in = (T)6 * cp.pure(1) + cp.kappa(1);
+        dg_out = (T)6 * cp.pure(0) + cp.kappa(0);
+        dinv_in = (T)1 / dg_in;
+        dinv_out = (T)1 / dg_out;
+    }
+    T acc0 = 0, acc1 = 0;
+
+    for (int k = k0; k < k1; ++k) {
+        const int base = k * sxy + j * sx;  // row j, plane k
+        T ym[VEC], yp[VEC], xv[VEC], zv[VEC];
+        uint32_t cym = 0;
+        if (grp_ok) {
+            // next plane of this row (streams from HBM)
+            ldv(base + sxy + ib, pn);
+            cn = cload<VEC>(A.code + base + sxy + ib);
+            // neighbouring rows of this plane (just streamed by other warps)
+            ldv(base - sx + ib, ym);
+            ldv(base + sx + ib, yp);
+            cym = cload<VEC>(A.code + base - sx + ib);
+            if (MODE == MODE_U) {
+                vload<T>(A.xv + base + ib, xv);
+                vload<T>(A.zv + base + ib, zv);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) pn[q] = ym[q] = yp[q] = 0;
+            cn = 0;
+        }
+        if (hl) {
+            ln = lds(base + sxy + i0 - 1);
+            lcn = A.code[base + sxy + i0 - 1];
+        }
+        if (hr) rn = lds(base + sxy + i0 + TXP);
+
+        T left = __shfl_up_sync(0xffffffffu, pc[VEC - 1], 1);
+        T right = __shfl_down_sync(0xffffffffu, pc[0], 1);
+        uint32_t lcode = __shfl_up_sync(0xffffffffu, cc >> (8 * (VEC - 1)), 1) & 0xffu;
+        if (lane == 0) {
+            left = lc;
+            lcode = lcc;
+        }
+        if (lane == 31) right = rc;
+        // code bytes of the -x neighbours of the lane's points
+        const uint32_t cxl = (VEC == 4) ? ((cc << 8) | lcode) : (((cc << 8) | lcode) & 0xffffu);
+        bool fast = false;
+        if (CP::kCompressed) {
+            const uint32_t special = (cc & CodeW<VEC>::rep(0x0Eu)) | (cxl & CodeW<VEC>::rep(0x02u)) |
+                                     (cym & CodeW<VEC>::rep(0x04u)) | (cm & CodeW<VEC>::rep(0x08u));
+            fast = !__any_sync(0xffffffffu, special != 0u);
+        }
+        T y[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const int i = ib + q;
+            const uint8_t c0 = (uint8_t)(cc >> (8 * q));
+            const T x0 = pc[q];
+            const T xl = q > 0 ? pc[q - 1] : left;
+            const T xr = q < VEC - 1 ? pc[q + 1] : right;
+            const T kp = cp.kappa(c0);
+            T ap, dinv, dg;
+            if (fast) {
+                const T wp = cp.pure(c0);
+                const T sum = ((x0 - xl) + (x0 - xr)) + ((x0 - ym[q]) + (x0 - yp[q])) +
+                              ((x0 - pm[q]) + (x0 - pn[q]));
+                ap = wp * sum + kp * x0;
+                dinv = (c0 & 1) ? dinv_in : dinv_out;
+                dg = (c0 & 1) ? dg_in : dg_out;
+            } else {
+                const int pl = base + i;
+                const T wxp = cp.w(0, i, j, k, pl, c0, c0);
+                const T wxm = cp.w(0, i - 1, j, k, pl - 1, (uint8_t)(cxl >> (8 * q)), c0);
+                const T wyp = cp.w(1, i, j, k, pl, c0, c0);
+                const T wym = cp.w(1, i, j - 1, k, pl - sx, (uint8_t)(cym >> (8 * q)), c0);
+                const T wzp = cp.w(2, i, j, k, pl, c0, c0);
+                const T wzm = cp.w(2, i, j, k - 1, pl - sxy, (uint8_t)(cm >> (8 * q)), c0);
+                ap = kp * x0;
+                ap += wxm * (x0 - xl);
+                ap += wxp * (x0 - xr);
+                ap += wym * (x0 - ym[q]);
+                ap += wyp * (x0 - yp[q]);
+                ap += wzm * (x0 - pm[q]);
+                ap += wzp * (x0 - pn[q]);
+                dg = ((((((wxm + wxp) + wym) + wyp) + wzm) + wzp) + kp);
+                dinv = (T)1 / dg;
+            }
+            const bool interior = grp_ok && i >= 1 && i <= g.nx - 2;
+            y[q] = interior ? ap : (T)0;
+            if (MODE == MODE_P) {
+                if (interior) acc0 += x0 * ap;
+            } else if (MODE == MODE_U) {
+                if (interior) {
+                    xv[q] = xv[q] + alpha * x0;
+                    const T znew = zv[q] - alpha * ap * dinv;
+                    zv[q] = znew;
+                    const T r = dg * znew;
+                    acc0 += r * znew;
+                    acc1 += r * r;
+                }
+            }
+        }
+        if (grp_ok) {
+            if (MODE == MODE_P) vstore<T>(A.out + base + ib, pc);
+            if (MODE == MODE_U) {
+                vstore<T>(A.xv + base + ib, xv);
+                vstore<T>(A.zv + base + ib, zv);
+            }
+            if (MODE == MODE_A) vstore<T>(A.out + base + ib, y);
+        }
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            pm[q] = pc[q];
+            pc[q] = pn[q];
+        }
+        cm = cc;
+        cc = cn;
+        lc = ln;
+        rc = rn;
+        lcc = lcn;
+    }
+    if (MODE == MODE_A) return;
+
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    double t0, t1;
+    if (MODE == MODE_P) {
+        if (last_block_total<NT, false>(A.st, A.partials, nb, (double)acc0, 0.0, sred, t0, t1)) {
+            if (threadIdx.x == 0) {
+                CgState *s = A.st;
+                s->sigma = t0;
+                if (s->profile) {
+                    s->alpha = isfinite(t0) && t0 != 0.0 ? s->rho / t0 : 0.0;
+                } else if (!(t0 > 0.0) || !isfinite(t0)) {
+                    s->done = 1;
+                    s->status = 1;
+                } else {
+                    s->alpha = s->rho / t0;
+                }
+                s->counter = 0;
+            }
+        }
+    } else {
+        if (last_block_total<NT, true>(A.st, A.partials, nb, (double)acc0, (double)acc1, sred, t0,
+                                       t1)) {
+            if (threadIdx.x == 0) {
+                CgState *s = A.st;
+                s->beta = t0 / s->rho;
+                s->rho = t0;
+                s->rr = t1;
+                s->iter += 1;
+                if (s->profile) {
+                    // timing run: keep going
+                } else if (!isfinite(t1)) {
+                    s->done = 1;
+                    s->status = 1;
+                } else if (t1 <= s->rr_stop) {
+                    s->done = 1;
+                    s->status = 0;
+                } else if (s->iter >= s->max_iter) {
+                    s->done = 1;
+                    s->status = 2;
+                }
+                s->counter = 0;
+            }
+        }
+    }
+}
+
+// FP64 true residual r = f - A phi on interior nodes (boundary neighbours
+// read their Dirichlet value through the lift already in f, so they are
+// masked here).  Writes z = r/diag to the padded solver layout (FP32 or FP64)
+// and reduces |r|^2 and r.z.
+template <typename TZ>
+__global__ void __launch_bounds__(256)
+k_residual(const double *__restrict__ phi, const double *__restrict__ f,
+           const double *__restrict__ Wx, const double *__restrict__ Wy,
+           const double *__restrict__ Wz, const double *__restrict__ diag, GridGeo g, PadGeo pg,
+           TZ *__restrict__ zout, CgState *st, double *partials) {
+    __shared__ double sred[8];
+    long long a = blockIdx.x * 256ll + threadIdx.x;
+    double rr = 0.0, rz = 0.0;
+    if (a < g.N) {
+        long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
+        bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+        long long pa = (k * g.ny + j) * pg.sx + i;
+        if (interior) {
+            long long sy = g.nx, sz = (long long)g.nx * g.ny;
+            double x0 = phi[a];
+            double s = diag[a] * x0;
+            if (i > 1) s -= Wx[a - 1] * phi[a - 1];
+            if (i < g.nx - 2) s -= Wx[a] * phi[a + 1];
+            if (j > 1) s -= Wy[a - sy] * phi[a - sy];
+            if (j < g.ny - 2) s -= Wy[a] * phi[a + sy];
+            if (k > 1) s -= Wz[a - sz] * phi[a - sz];
+            if (k < g.nz - 2) s -= Wz[a] * phi[a + sz];
+            double r = f[a] - s;
+            TZ z;
+            if (sizeof(TZ) == 4) z = (TZ)((float)r / (float)diag[a]);
+            else z = (TZ)(r / diag[a]);
+            zout[pa] = z;
+            rr = r * r;
+            rz = r * (double)z;
+        }
+    }
+    int nb = gridDim.x;
+    double t0, t1;
+    if (last_block_total<256, true>(st, partials, nb, rr, rz, sred, t0, t1)) {
+        if (threadIdx.x == 0) {
+            st->res64 = t0;
+            st->rz64 = t1;
+            st->counter = 0;
+        }
+    }
+}
+
+// phi(interior) += x (padded)
+template <typename TX>
+__global__ void k_promote(double *__restrict__ phi, const TX *__restrict__ x, GridGeo g, PadGeo pg) {
+    long long a = blockIdx.x * 256ll + threadIdx.x;
+    if (a >= g.N) return;
+    long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
+    bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+    if (interior) phi[a] += (double)x[(k * g.ny + j) * pg.sx + i];
+}
+
+template <typename T>
+__global__ void k_canon_to_pad(const T *__restrict__ src, T *__restrict__ dst, GridGeo g, PadGeo pg) {
+    long long a = blockIdx.x * 256ll + threadIdx.x;
+    if (a >= g.N) return;
+    long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
+    bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+    dst[(k * g.ny + j) * pg.sx + i] = interior ? src[a] : (T)0;
+}
+
+template <typename T>
+__global__ void k_pad_to_canon(const T *__restrict__ src, T *__restrict__ dst, GridGeo g, PadGeo pg) {
+    long long a = blockIdx.x * 256ll + threadIdx.x;
+    if (a >= g.N) return;
+    long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
+    bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+    dst[a] = interior ? src[(k * g.ny + j) * pg.sx + i] : (T)0;
+}
+
+constexpr int TYC = 8;  // rows (warps) per stencil block
+// resident blocks per SM the register allocation must allow
+template <typename T>
+struct MinB {
+    static constexpr int v = sizeof(T) == 4 ? 4 : 3;
+};
+
+template <typename T>
+dim3 stencil_grid(const PadGeo &g, int KC) {
+    constexpr int TXP = 32 * VT<T>::N;
+    return dim3((unsigned)cdiv(g.nx - 1, TXP), (unsigned)cdiv(g.ny - 2, TYC),
+                (unsigned)cdiv(g.nz - 2, KC));
+}
+
+// z-chunk length: trade the two extra planes each chunk reads against the
+// tail of the last wave (blocks resident per SM from the occupancy API).
+template <typename T, class CP>
+int choose_kc(const PadGeo &g) {
+    static int resident = 0;
+    if (!resident) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_stencil<T, CP, MODE_U, TYC, MinB<T>::v>, 32 * TYC, 0) != cudaSuccess ||
+            per_sm <= 0) {
+            cudaGetLastError();
+            per_sm = MinB<T>::v;
+        }
+        resident = per_sm * num_sms();
+    }
+    long long cols = (long long)cdiv(g.nx - 1, 32 * VT<T>::N) * cdiv(g.ny - 2, TYC);
+    int best = 8;
+    double best_eff = -1.0;
+    for (int kc = 4; kc <= 64; ++kc) {
+        long long blocks = cols * cdiv(g.nz - 2, kc);
+        double waves = (double)blocks / resident;
+        double occ = waves / ceil(waves);
+        double stream = (double)kc / (kc + 1.0);  // about half the streamed arrays re-read 2 planes
+        double eff = occ * stream;
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = kc;
+        }
+    }
+    return best;
+}
+
+int default_kc(const PadGeo &g, int precision) {
+    return precision == PB_MIXED ? choose_kc<float, CoefC32>(g) : choose_kc<double, CoefS64>(g);
+}
+
+CoefC32 make_c32(const pb_system *sys) {
+    const pb_grid *g = sys->g;
+    CoefC32 c;
+    c.wx = sys->w32[0];
+    c.wy = sys->w32[1];
+    c.wz = sys->w32[2];
+    c.w_in = (float)(sys->p.eps_in * g->geo.h);
+    c.w_out = (float)(sys->p.eps_out * g->geo.h);
+    c.kap = (float)sys->kap_s;
+    return c;
+}
+
+CoefS64 make_s64(const pb_system *sys) {
+    CoefS64 c;
+    c.W0 = sys->W[0];
+    c.W1 = sys->W[1];
+    c.W2 = sys->W[2];
+    c.kap = sys->kap_s;
+    c.nx = sys->g->geo.nx;
+    c.ny = sys->g->geo.ny;
+    return c;
+}
+
+template <typename T, class CP>
+pb_status launch_iter(pb_system *sys, const CP &cp, const T *z, const T *pold, T *pnew, T *x,
+                      T *zmut, int KC, cudaStream_t s) {
+    dim3 grid = stencil_grid<T>(sys->pad, KC);
+    KArgs<T> a{};
+    a.code = sys->code;
+    a.st = sys->st;
+    a.partials = sys->partials;
+    a.pg = sys->pad;
+    a.KC = KC;
+    a.in = z;
+    a.in2 = pold;
+    a.out = pnew;
+    k_stencil<T, CP, MODE_P, TYC, MinB<T>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
+    KArgs<T> b = a;
+    b.in = pnew;
+    b.in2 = nullptr;
+    b.out = nullptr;
+    b.xv = x;
+    b.zv = zmut;
+    k_stencil<T, CP, MODE_U, TYC, MinB<T>::v><<<grid, 32 * TYC, 0, s>>>(b, cp);
+    return PB_OK;
+}
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+pb_status sync_state(pb_system *sys, cudaStream_t s) {
+    PB_CUDA_TRY(cudaMemcpyAsync(sys->h_st, sys->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return PB_OK;
+}
+
+pb_status residual(pb_system *sys, bool fp32_out, cudaStream_t s) {
+    const GridGeo &g = sys->g->geo;
+    unsigned blocks = cdiv(g.N, 256);
+    if (fp32_out)
+        k_residual<float><<<blocks, 256, 0, s>>>(sys->phi, sys->rhs, sys->W[0], sys->W[1], sys->W[2],
+                                                 sys->diag, g, sys->pad, sys->z32, sys->st,
+                                                 sys->partials);
+    else
+        k_residual<double><<<blocks, 256, 0, s>>>(sys->phi, sys->rhs, sys->W[0], sys->W[1],
+                                                  sys->W[2], sys->diag, g, sys->pad, sys->z64,
+                                                  sys->st, sys->partials);
+    PB_LAUNCH_CHECK();
+    return PB_OK;
+}
+
+// Runs PCG iterations until the device state says done; host polls a pinned
+// copy of the state after every chunk, keeping two chunks in flight.
+template <typename T, class CP>
+pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC, int chunk,
+                  double deadline, cudaStream_t s, int *iters_out) {
+    T *bufs[2] = {pa, pb};
+    int cur = 0;  // index of p_old
+    cudaEvent_t ev[2];
+    PB_CUDA_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    PB_CUDA_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    CgState *hs = sys->h_st;  // two slots: hs[0], hs[1]
+    pb_status rc = PB_OK;
+    auto issue = [&](int slot) -> pb_status {
+        for (int c = 0; c < chunk; ++c) {
+            launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
+            cur ^= 1;
+        }
+        note_launch(2 * chunk - 1);
+        PB_LAUNCH_CHECK();
+        PB_CUDA_TRY(cudaMemcpyAsync(hs + slot, sys->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        PB_CUDA_TRY(cudaEventRecord(ev[slot], s));
+        return PB_OK;
+    };
+    int slot = 0;
+    // every chunk advances the device iteration count by `chunk` unless the
+    // state is done, so this many chunks always suffice
+    long long max_chunks = (long long)hs[2].max_iter / chunk + 4;
+    long long issued = 0;
+    if ((rc = issue(0)) != PB_OK) goto out;
+    if ((rc = issue(1)) != PB_OK) goto out;
+    issued = 2;
+    for (;;) {
+        cudaError_t e = cudaEventSynchronize(ev[slot]);
+        if (e != cudaSuccess) {
+            set_error("PCG chunk failed: %s", cudaGetErrorString(e));
+            rc = PB_ERR_CUDA;
+            break;
+        }
+        if (hs[slot].done) break;
+        if (deadline > 0.0 && now_s() > deadline) {
+            rc = PB_ERR_TIMEOUT;
+            break;
+        }
+        if (++issued > max_chunks) {
+            set_error("PCG state stopped advancing");
+            rc = PB_ERR_CUDA;
+            break;
+        }
+        if ((rc = issue(slot)) != PB_OK) break;
+        slot ^= 1;
+    }
+out:
+    // drain and read the final state
+    {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("PCG failed: %s", cudaGetErrorString(e));
+            rc = PB_ERR_CUDA;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc == PB_OK) {
+        pb_status r2 = sync_state(sys, s);
+        if (r2 != PB_OK) return r2;
+        *iters_out = hs[0].iter;
+    }
+    return rc;
+}
+
+pb_status init_state(pb_system *sys, double rho, double rr0, double rr_stop, int max_iter,
+                     cudaStream_t s, int profile = 0) {
+    CgState h{};
+    h.profile = profile;
+    h.rho = rho;
+    h.rr0 = rr0;
+    h.rr = rr0;
+    h.rr_stop = rr_stop;
+    h.beta = 0.0;
+    h.alpha = 0.0;
+    h.iter = 0;
+    h.max_iter = max_iter;
+    h.done = 0;
+    h.status = 0;
+    h.counter = 0;
+    // staged through the pinned mirror so the copy is stream-ordered
+    CgState *stage = sys->h_st + 2;
+    *stage = h;
+    PB_CUDA_TRY(cudaMemcpyAsync(sys->st, stage, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    PB_CUDA_TRY(cudaStreamSynchronize(s));
+    return PB_OK;
+}
+
+}  // namespace
+
+pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s) {
+    const PadGeo &p = sys->pad;
+    if (!sys->st) {
+        sys->st = (CgState *)dalloc(sizeof(CgState), s);
+        if (!sys->st) return PB_ERR_OOM;
+        PB_CUDA_TRY(cudaMemsetAsync(sys->st, 0, sizeof(CgState), s));
+        PB_CUDA_TRY(cudaMallocHost((void **)&sys->h_st, 4 * sizeof(CgState)));
+        dim3 g32 = stencil_grid<float>(p, 4), g64 = stencil_grid<double>(p, 4);
+        long long nb = std::max<long long>((long long)g32.x * g32.y * g32.z,
+                                           (long long)g64.x * g64.y * g64.z);
+        nb = std::max<long long>(nb, cdiv(p.N, 256));
+        sys->npartials = (int)(2 * nb + 64);
+        sys->partials = (double *)dalloc(sizeof(double) * sys->npartials, s);
+        if (!sys->partials) return PB_ERR_OOM;
+    }
+    size_t bytes32 = sizeof(float) * (size_t)p.Np, bytes64 = sizeof(double) * (size_t)p.Np;
+    if (precision == PB_MIXED && !sys->z32) {
+        sys->z32 = (float *)dalloc(bytes32, s);
+        sys->pa32 = (float *)dalloc(bytes32, s);
+        sys->pb32 = (float *)dalloc(bytes32, s);
+        sys->d32 = (float *)dalloc(bytes32, s);
+        if (!sys->z32 || !sys->pa32 || !sys->pb32 || !sys->d32) return PB_ERR_OOM;
+        PB_CUDA_TRY(cudaMemsetAsync(sys->z32, 0, bytes32, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->pa32, 0, bytes32, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->pb32, 0, bytes32, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->d32, 0, bytes32, s));
+    }
+    if (precision == PB_FP64 && !sys->z64) {
+        sys->z64 = (double *)dalloc(bytes64, s);
+        sys->pa64 = (double *)dalloc(bytes64, s);
+        sys->pb64 = (double *)dalloc(bytes64, s);
+        sys->x64 = (double *)dalloc(bytes64, s);
+        if (!sys->z64 || !sys->pa64 || !sys->pb64 || !sys->x64) return PB_ERR_OOM;
+        PB_CUDA_TRY(cudaMemsetAsync(sys->z64, 0, bytes64, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->pa64, 0, bytes64, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->pb64, 0, bytes64, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->x64, 0, bytes64, s));
+    }
+    return PB_OK;
+}
+
+pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve_stats *stats) {
+    double t_start = now_s();
+    double deadline = o->time_budget_s > 0.0 ? t_start + o->time_budget_s : 0.0;
+    const GridGeo &g = sys->g->geo;
+    const PadGeo &p = sys->pad;
+    pb_status rc = ensure_solver_ws(sys, o->precision, s);
+    if (rc != PB_OK) return rc;
+    int KC = default_kc(p, o->precision);
+    int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
+    int max_outer = o->max_outer > 0 ? o->max_outer : 30;
+    double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
+    double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
+    int chunk = 16;
+
+    // phi = boundary values, interior 0 (zero initial guess)
+    PB_CUDA_TRY(cudaMemcpyAsync(sys->phi, sys->bc, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, s));
+    int iters = 0, outer = 0;
+    int status = PB_OK;
+    double fn2 = 0.0, res2 = 0.0;
+    if (o->precision == PB_MIXED) {
+        if ((rc = residual(sys, true, s)) != PB_OK) return rc;
+        if ((rc = sync_state(sys, s)) != PB_OK) return rc;
+        fn2 = sys->h_st->res64;
+        res2 = fn2;
+        outer = 1;
+        CoefC32 cp = make_c32(sys);
+        int stagnant = 0;
+        while (fn2 > 0.0 && res2 > rtol * rtol * fn2) {
+            if (outer > max_outer || iters >= max_iter) {
+                status = PB_ERR_NOCONV;
+                break;
+            }
+            double rel = sqrt(res2 / fn2);
+            double itol = std::max(inner_rtol, 0.5 * rtol / rel);
+            if (itol > 0.5) itol = 0.5;
+            double rz = sys->h_st->rz64;
+            if ((rc = init_state(sys, rz, res2, itol * itol * res2, max_iter - iters, s)) != PB_OK)
+                return rc;
+            size_t bytes32 = sizeof(float) * (size_t)p.Np;
+            PB_CUDA_TRY(cudaMemsetAsync(sys->d32, 0, bytes32, s));
+            PB_CUDA_TRY(cudaMemsetAsync(sys->pa32, 0, bytes32, s));
+            int it = 0;
+            rc = run_pcg<float, CoefC32>(sys, cp, sys->z32, sys->pa32, sys->pb32, sys->d32, KC, chunk,
+                                         deadline, s, &it);
+            if (rc == PB_ERR_TIMEOUT) {
+                status = PB_ERR_TIMEOUT;
+            } else if (rc != PB_OK) {
+                return rc;
+            }
+            if (rc == PB_OK) iters += it;
+            k_promote<float><<<cdiv(g.N, 256), 256, 0, s>>>(sys->phi, sys->d32, g, p);
+            PB_LAUNCH_CHECK();
+            if ((rc = residual(sys, true, s)) != PB_OK) return rc;
+            if ((rc = sync_state(sys, s)) != PB_OK) return rc;
+            double prev = res2;
+            res2 = sys->h_st->res64;
+            ++outer;
+            if (status == PB_ERR_TIMEOUT) break;
+            if (res2 > 0.25 * prev) {
+                if (++stagnant >= 3) {
+                    status = PB_ERR_NOCONV;
+                    break;
+                }
+            } else {
+                stagnant = 0;
+            }
+        }
+    } else {
+        // plain FP64 PCG on the whole system, restarted from the true
+        // residual if the recursive one drifted
+        CoefS64 cp = make_s64(sys);
+        size_t bytes64 = sizeof(double) * (size_t)p.Np;
+        PB_CUDA_TRY(cudaMemsetAsync(sys->x64, 0, bytes64, s));
+        if ((rc = residual(sys, false, s)) != PB_OK) return rc;
+        if ((rc = sync_state(sys, s)) != PB_OK) return rc;
+        fn2 = sys->h_st->res64;
+        res2 = fn2;
+        outer = 1;
+        while (fn2 > 0.0 && res2 > rtol * rtol * fn2) {
+            if (outer > max_outer || iters >= max_iter) {
+                status = PB_ERR_NOCONV;
+                break;
+            }
+            double rz = sys->h_st->rz64;
+            if ((rc = init_state(sys, rz, res2, rtol * rtol * fn2 * 0.25, max_iter - iters, s)) != PB_OK)
+                return rc;
+            PB_CUDA_TRY(cudaMemsetAsync(sys->pa64, 0, bytes64, s));
+            int it = 0;
+            rc = run_pcg<double, CoefS64>(sys, cp, sys->z64, sys->pa64, sys->pb64, sys->x64, KC,
+                                          chunk, deadline, s, &it);
+            if (rc == PB_ERR_TIMEOUT) status = PB_ERR_TIMEOUT;
+            else if (rc != PB_OK) return rc;
+            if (rc == PB_OK) iters += it;
+            PB_CUDA_TRY(cudaMemcpyAsync(sys->phi, sys->bc, sizeof(double) * g.N,
+                                        cudaMemcpyDeviceToDevice, s));
+            k_promote<double><<<cdiv(g.N, 256), 256, 0, s>>>(sys->phi, sys->x64, g, p);
+            PB_LAUNCH_CHECK();
+            if ((rc = residual(sys, false, s)) != PB_OK) return rc;
+            if ((rc = sync_state(sys, s)) != PB_OK) return rc;
+            res2 = sys->h_st->res64;
+            ++outer;
+            if (status == PB_ERR_TIMEOUT) break;
+        }
+    }
+    sys->fnorm2 = fn2;
+    sys->solved = 1;
+    if (stats) {
+        stats->status = status;
+        stats->iters_inner = iters;
+        stats->iters_outer = outer;
+        stats->true_rel_res = fn2 > 0.0 ? sqrt(res2 / fn2) : 0.0;
+        stats->seconds = now_s() - t_start;
+        stats->dof = (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+        // FP32: P reads z,p_old writes p; U reads p,x,z writes x,z (+2 code bytes);
+        // FP64 plain: same vectors plus three weight arrays streamed twice.
+        long long per = o->precision == PB_MIXED ? (8 * 4 + 2) : (8 * 8 + 6 * 8 + 2);
+        stats->model_bytes = (long long)iters * stats->dof * per + (long long)outer * g.N * 64;
+    }
+    return (pb_status)status;
+}
+
+pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cudaStream_t s) {
+    if (precision == PB_MIXED && !sys->z32) {
+        set_error("no mixed-precision solver state");
+        return PB_ERR_STATE;
+    }
+    if (precision == PB_FP64 && !sys->z64) {
+        set_error("no FP64 solver state");
+        return PB_ERR_STATE;
+    }
+    pb_status rc = init_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1);
+    if (rc != PB_OK) return rc;
+    int KC = default_kc(sys->pad, precision);
+    for (int r = 0; r < reps; ++r) {
+        if (precision == PB_MIXED) {
+            CoefC32 cp = make_c32(sys);
+            dim3 grid = stencil_grid<float>(sys->pad, KC);
+            KArgs<float> a{};
+            a.code = sys->code;
+            a.st = sys->st;
+            a.partials = sys->partials;
+            a.pg = sys->pad;
+            a.KC = KC;
+            if (which == 0 || which == 2) {
+                a.in = sys->z32;
+                a.in2 = (r & 1) ? sys->pb32 : sys->pa32;
+                a.out = (r & 1) ? sys->pa32 : sys->pb32;
+                k_stencil<float, CoefC32, MODE_P, TYC, MinB<float>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
+                PB_LAUNCH_CHECK();
+            }
+            if (which == 1 || which == 2) {
+                a.in = (r & 1) ? sys->pa32 : sys->pb32;
+                a.in2 = nullptr;
+                a.out = nullptr;
+                a.xv = sys->d32;
+                a.zv = sys->z32;
+                k_stencil<float, CoefC32, MODE_U, TYC, MinB<float>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
+                PB_LAUNCH_CHECK();
+            }
+        } else {
+            CoefS64 cp = make_s64(sys);
+            dim3 grid = stencil_grid<double>(sys->pad, KC);
+            KArgs<double> a{};
+            a.code = sys->code;
+            a.st = sys->st;
+            a.partials = sys->partials;
+            a.pg = sys->pad;
+            a.KC = KC;
+            if (which == 0 || which == 2) {
+                a.in = sys->z64;
+                a.in2 = (r & 1) ? sys->pb64 : sys->pa64;
+                a.out = (r & 1) ? sys->pa64 : sys->pb64;
+                k_stencil<double, CoefS64, MODE_P, TYC, MinB<double>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
+                PB_LAUNCH_CHECK();
+            }
+            if (which == 1 || which == 2) {
+                a.in = (r & 1) ? sys->pa64 : sys->pb64;
+                a.in2 = nullptr;
+                a.out = nullptr;
+                a.xv = sys->x64;
+                a.zv = sys->z64;
+                k_stencil<double, CoefS64, MODE_U, TYC, MinB<double>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
+                PB_LAUNCH_CHECK();
+            }
+        }
+    }
+    // phi is untouched: only the solver workspace (z, p, x increment) changed
+    return PB_OK;
+}
+
+pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaStream_t s) {
+    const GridGeo &g = sys->g->geo;
+    const PadGeo &p = sys->pad;
+    int KC = default_kc(p, precision);
+    size_t esz = precision == PB_MIXED ? 4 : 8;
+    void *xp = dalloc(esz * (size_t)p.Np, s), *yp = dalloc(esz * (size_t)p.Np, s);
+    if (!xp || !yp) return PB_ERR_OOM;
+    PB_CUDA_TRY(cudaMemsetAsync(xp, 0, esz * (size_t)p.Np, s));
+    PB_CUDA_TRY(cudaMemsetAsync(yp, 0, esz * (size_t)p.Np, s));
+    unsigned blocks = cdiv(g.N, 256);
+    if (precision == PB_MIXED) {
+        k_canon_to_pad<float><<<blocks, 256, 0, s>>>((const float *)x, (float *)xp, g, p);
+        KArgs<float> a{};
+        a.in = (const float *)xp;
+        a.out = (float *)yp;
+        a.code = sys->code;
+        a.pg = p;
+        a.KC = KC;
+        k_stencil<float, CoefC32, MODE_A, TYC, MinB<float>::v><<<stencil_grid<float>(p, KC), 32 * TYC, 0, s>>>(
+            a, make_c32(sys));
+        k_pad_to_canon<float><<<blocks, 256, 0, s>>>((const float *)yp, (float *)y, g, p);
+    } else {
+        k_canon_to_pad<double><<<blocks, 256, 0, s>>>((const double *)x, (double *)xp, g, p);
+        KArgs<double> a{};
+        a.in = (const double *)xp;
+        a.out = (double *)yp;
+        a.code = sys->code;
+        a.pg = p;
+        a.KC = KC;
+        k_stencil<double, CoefS64, MODE_A, TYC, MinB<double>::v><<<stencil_grid<double>(p, KC), 32 * TYC, 0, s>>>(
+            a, make_s64(sys));
+        k_pad_to_canon<double><<<blocks, 256, 0, s>>>((const double *)yp, (double *)y, g, p);
+    }
+    note_launch(2);
+    PB_LAUNCH_CHECK();
+    dfree(xp, s);
+    dfree(yp, s);
+    return PB_OK;
+}
+
+}  // namespace pbg
