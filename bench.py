@@ -351,7 +351,10 @@ def run_ours(args, wl):
             traffic = json.load(fh).get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_stencil<float,CoefC32,MODE_U> (FP32 PCG update)",
+                "kernel": ("k_stencil_tma<MODE_U> (FP32 PCG update, TMA-staged)"
+                           if stats[-1]["kc"] >= 1000 else
+                           "k_stencil<float,CoefC32,MODE_U> (FP32 PCG update)"),
+                "z_chunk": stats[-1]["kc"] % 1000,
                 "alg_bytes_per_launch": bytes_u, "launch_s": kt["update"],
                 "peak_kind": f"{peak_kind} hbm_gbs",
                 "direction_kernel": {"launch_s": kt["direction"],

@@ -128,6 +128,7 @@ typedef struct {
     int32_t status;           /* pb_status of the solve                     */
     int32_t iters_inner;      /* PCG iterations (FP32 inner or FP64 plain)  */
     int32_t iters_outer;      /* FP64 residual evaluations                  */
+    int32_t kc;               /* tuned kernel: z-chunk + 1000 * variant     */
     double true_rel_res;      /* ||f - A phi|| / ||f|| in FP64 at exit      */
     double seconds;           /* host wall time of the call                 */
     int64_t dof;              /* interior unknowns                          */
@@ -257,6 +258,12 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
  * Needs a prior pb_solve in that precision (PB_ERR_STATE otherwise). */
 pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int32_t reps,
                              void *stream);
+
+/* pb_set_tuning -- fix the PCG kernel variant (0: register-pipelined warps,
+ * 1: TMA-staged, FP32 only) and z-chunk length (planes per block) used for
+ * every system with s's grid shape and this precision, instead of the
+ * autotuner's choice (which times the candidates on first use of a shape). */
+pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_t z_chunk);
 
 /* Number of CUDA kernels launched by this library in this process so far. */
 int64_t pb_kernel_launches(void);

@@ -28,7 +28,7 @@ __all__ = [
     "GridSpec", "Params", "SolveOpts", "Grid", "System",
     "pb_build_grid", "pb_assemble_coeffs", "pb_coulomb_terms", "pb_solve", "pb_energy",
     "pb_get_array", "pb_get_phi", "pb_apply", "pb_solve_batch", "pb_last_error",
-    "pb_profile_kernels", "pb_kernel_launches",
+    "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning",
     "solve_molecule", "library_path", "loaded", "PBError",
 ]
 
@@ -321,6 +321,10 @@ def pb_solve_batch(systems, opts: SolveOpts, stream=None) -> list:
 def pb_profile_kernels(system: System, precision: int, which: int, reps: int, stream=None) -> None:
     N.check(N.lib().pb_profile_kernels(system.handle, int(precision), int(which), int(reps),
                                        _stream(stream)))
+
+
+def pb_set_tuning(system: System, precision: int, variant: int, z_chunk: int) -> None:
+    N.check(N.lib().pb_set_tuning(system.handle, int(precision), int(variant), int(z_chunk)))
 
 
 def pb_kernel_launches() -> int:

@@ -43,7 +43,7 @@ class SolveOptsC(C.Structure):
 
 class SolveStatsC(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters_inner", C.c_int32), ("iters_outer", C.c_int32),
-                ("true_rel_res", C.c_double), ("seconds", C.c_double), ("dof", C.c_int64),
+                ("kc", C.c_int32), ("true_rel_res", C.c_double), ("seconds", C.c_double), ("dof", C.c_int64),
                 ("model_bytes", C.c_int64)]
 
 
@@ -79,6 +79,7 @@ SIGNATURES = {
     "pb_solve_batch": (C.c_int, [P, C.c_int32, P, P, P]),
     "pb_profile_kernels": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P]),
     "pb_kernel_launches": (C.c_int64, []),
+    "pb_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "pb_last_error": (C.c_char_p, []),
     "pb_version": (C.c_char_p, []),
 }

@@ -273,6 +273,7 @@ void pb_system_free(pb_system *s) {
                     s->partials, s->st, s->Phi, s->Psi, s->ecoul_phi, s->eacc};
     for (void *p : ptrs) dfree(p, st);
     cudaStreamSynchronize(st);
+    free_tma_state(s);
     if (s->h_st) cudaFreeHost(s->h_st);
     if (s->h_energy) cudaFreeHost(s->h_energy);
     delete s;
@@ -555,5 +556,14 @@ pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int
 }
 
 int64_t pb_kernel_launches(void) { return g_launches.load(); }
+
+pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_t z_chunk) {
+    set_error("");
+    if (!s || (precision != PB_FP64 && precision != PB_MIXED)) {
+        set_error("pb_set_tuning: bad argument");
+        return PB_ERR_ARG;
+    }
+    return set_tuning(s, precision, variant, z_chunk);
+}
 
 }  // extern "C"

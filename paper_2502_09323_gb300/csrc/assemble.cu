@@ -215,7 +215,7 @@ pb_status assemble(pb_system *sys, cudaStream_t s) {
     p.nx = geo.nx;
     p.ny = geo.ny;
     p.nz = geo.nz;
-    p.sx = (geo.nx + 3) & ~3;
+    p.sx = (geo.nx + 15) & ~15;  // 16 elements: TMA strides and code rows need 16 B
     p.sxy = (long long)p.sx * geo.ny;
     p.Np = p.sxy * geo.nz;
     p.N = N;

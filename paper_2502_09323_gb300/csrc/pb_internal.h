@@ -157,6 +157,7 @@ struct pb_system {
     pb_energy_terms *h_energy;  // pinned
     int solved, have_surface, have_pairs;
     double fnorm2;
+    void *tma;          // tensor maps of the FP32 stencil kernels (host object)
 };
 
 namespace pbg {
@@ -179,6 +180,8 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
 pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaStream_t s);
 pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s);
 pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cudaStream_t s);
+void free_tma_state(pb_system *sys);
+pb_status set_tuning(pb_system *sys, int precision, int variant, int kc);
 
 // ------------------------------------------------------------- energy.cu --
 pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);

@@ -23,8 +23,16 @@
 // six weights and the node's ionic term, so no coefficient array is streamed.
 #include <math.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <type_traits>
 
 #include "pb_internal.h"
 
@@ -248,25 +256,47 @@ k_stencil(KArgs<T> A, CP cp) {
         return v;
     };
 
+    // Software pipeline.  Entering iteration k (output plane k) registers
+    // hold: own row at planes k-1, k, k+1 (pm, pc, pn); neighbour rows j-1,
+    // j+1 at plane k (ym, yp); x and z at plane k (U mode).  Iteration k
+    // issues the loads of plane k+2 (own row, raw) and plane k+1 (neighbour
+    // rows, x, z) before computing plane k, so every load has a full
+    // iteration to arrive.
     T pm[VEC], pc[VEC], pn[VEC];
-    uint32_t cm = 0, cc = 0, cn = 0;
+    T ym[VEC], yp[VEC], xv[VEC], zv[VEC];
+    uint32_t cm = 0, cc = 0, cn = 0, cym = 0;
     T lc = 0, rc = 0, ln = 0, rn = 0;
     uint32_t lcc = 0, lcn = 0;
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) pm[q] = pc[q] = pn[q] = 0;
+    for (int q = 0; q < VEC; ++q) pm[q] = pc[q] = pn[q] = ym[q] = yp[q] = xv[q] = zv[q] = 0;
     if (grp_ok) {
         const int b0 = (k0 - 1) * sxy + j * sx + ib;
         ldv(b0, pm);
         cm = cload<VEC>(A.code + b0);
         ldv(b0 + sxy, pc);
         cc = cload<VEC>(A.code + b0 + sxy);
+        ldv(b0 + 2 * sxy, pn);
+        cn = cload<VEC>(A.code + b0 + 2 * sxy);
+        ldv(b0 + sxy - sx, ym);
+        ldv(b0 + sxy + sx, yp);
+        cym = cload<VEC>(A.code + b0 + sxy - sx);
+        if (MODE == MODE_U) {
+            vload<T>(A.xv + b0 + sxy, xv);
+            vload<T>(A.zv + b0 + sxy, zv);
+        }
     }
     if (hl) {
         const int q0 = k0 * sxy + j * sx + i0 - 1;
         lc = lds(q0);
         lcc = A.code[q0];
+        ln = lds(q0 + sxy);
+        lcn = A.code[q0 + sxy];
     }
-    if (hr) rc = lds(k0 * sxy + j * sx + i0 + TXP);
+    if (hr) {
+        const int q0 = k0 * sxy + j * sx + i0 + TXP;
+        rc = lds(q0);
+        rn = lds(q0 + sxy);
+    }
 
     // fast-path diagonals of the two pure media and their inverses
     T dg_in = 1, dg_out = 1, dinv_in = 1, dinv_out = 1;
@@ -280,31 +310,39 @@ k_stencil(KArgs<T> A, CP cp) {
 
     for (int k = k0; k < k1; ++k) {
         const int base = k * sxy + j * sx;  // row j, plane k
-        T ym[VEC], yp[VEC], xv[VEC], zv[VEC];
-        uint32_t cym = 0;
-        if (grp_ok) {
-            // next plane of this row (streams from HBM)
-            ldv(base + sxy + ib, pn);
-            cn = cload<VEC>(A.code + base + sxy + ib);
-            // neighbouring rows of this plane (just streamed by other warps)
-            ldv(base - sx + ib, ym);
-            ldv(base + sx + ib, yp);
-            cym = cload<VEC>(A.code + base - sx + ib);
+        const bool more = k + 1 < k1;
+        // ---- issue next loads
+        T n2a[VEC], n2b[VEC];  // own row, plane k+2 (raw: z and p_old in P mode)
+        T ymn[VEC], ypn[VEC], xvn[VEC], zvn[VEC];
+        uint32_t cn2 = 0, cymn = 0;
+        T ln2a = 0, ln2b = 0, rn2a = 0, rn2b = 0;
+        uint32_t lcn2 = 0;
+        if (grp_ok && more) {
+            const int q2 = base + 2 * sxy + ib;
+            vload<T>(A.in + q2, n2a);
+            if (MODE == MODE_P) vload<T>(A.in2 + q2, n2b);
+            cn2 = cload<VEC>(A.code + q2);
+            ldv(base + sxy - sx + ib, ymn);
+            ldv(base + sxy + sx + ib, ypn);
+            cymn = cload<VEC>(A.code + base + sxy - sx + ib);
             if (MODE == MODE_U) {
-                vload<T>(A.xv + base + ib, xv);
-                vload<T>(A.zv + base + ib, zv);
+                vload<T>(A.xv + base + sxy + ib, xvn);
+                vload<T>(A.zv + base + sxy + ib, zvn);
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) pn[q] = ym[q] = yp[q] = 0;
-            cn = 0;
         }
-        if (hl) {
-            ln = lds(base + sxy + i0 - 1);
-            lcn = A.code[base + sxy + i0 - 1];
+        if (hl && more) {
+            const int q2 = base + 2 * sxy + i0 - 1;
+            ln2a = A.in[q2];
+            if (MODE == MODE_P) ln2b = A.in2[q2];
+            lcn2 = A.code[q2];
         }
-        if (hr) rn = lds(base + sxy + i0 + TXP);
+        if (hr && more) {
+            const int q2 = base + 2 * sxy + i0 + TXP;
+            rn2a = A.in[q2];
+            if (MODE == MODE_P) rn2b = A.in2[q2];
+        }
 
+        // ---- compute plane k
         T left = __shfl_up_sync(0xffffffffu, pc[VEC - 1], 1);
         T right = __shfl_down_sync(0xffffffffu, pc[0], 1);
         uint32_t lcode = __shfl_up_sync(0xffffffffu, cc >> (8 * (VEC - 1)), 1) & 0xffu;
@@ -379,16 +417,29 @@ k_stencil(KArgs<T> A, CP cp) {
             }
             if (MODE == MODE_A) vstore<T>(A.out + base + ib, y);
         }
+        // ---- rotate the pipeline
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
             pm[q] = pc[q];
             pc[q] = pn[q];
+            pn[q] = (MODE == MODE_P) ? n2a[q] + beta * n2b[q] : n2a[q];
+            ym[q] = ymn[q];
+            yp[q] = ypn[q];
+            if (MODE == MODE_U) {
+                xv[q] = xvn[q];
+                zv[q] = zvn[q];
+            }
         }
         cm = cc;
         cc = cn;
+        cn = cn2;
+        cym = cymn;
         lc = ln;
         rc = rn;
         lcc = lcn;
+        ln = (MODE == MODE_P) ? ln2a + beta * ln2b : ln2a;
+        rn = (MODE == MODE_P) ? rn2a + beta * rn2b : rn2a;
+        lcn = lcn2;
     }
     if (MODE == MODE_A) return;
 
@@ -436,6 +487,8 @@ k_stencil(KArgs<T> A, CP cp) {
         }
     }
 }
+
+#include "stencil_tma.cuh"
 
 // FP64 true residual r = f - A phi on interior nodes (boundary neighbours
 // read their Dirichlet value through the lift already in f, so they are
@@ -516,7 +569,7 @@ constexpr int TYC = 8;  // rows (warps) per stencil block
 // resident blocks per SM the register allocation must allow
 template <typename T>
 struct MinB {
-    static constexpr int v = sizeof(T) == 4 ? 4 : 3;
+    static constexpr int v = sizeof(T) == 4 ? 3 : 2;
 };
 
 template <typename T>
@@ -560,6 +613,160 @@ int choose_kc(const PadGeo &g) {
 
 int default_kc(const PadGeo &g, int precision) {
     return precision == PB_MIXED ? choose_kc<float, CoefC32>(g) : choose_kc<double, CoefS64>(g);
+}
+
+// ------------------------------------------------------ TMA tensor maps --
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D tiled map over a padded (sx, ny, nz) array; box (bw, bh, 1)
+pb_status make_map(CUtensorMap *m, const void *base, bool bytes, const PadGeo &g, int bw, int bh) {
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return PB_ERR_CUDA;
+    }
+    const uint64_t esz = bytes ? 1 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)g.sx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)g.sx * esz, (cuuint64_t)g.sxy * esz};
+    cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return PB_ERR_CUDA;
+    }
+    return PB_OK;
+}
+
+// maps of one TMA stencil launch
+pb_status tma_maps(const pb_system *sys, int mode, const float *a, const float *b, const float *x,
+                   const float *z, tma::Maps *m) {
+    const PadGeo &g = sys->pad;
+    pb_status rc = make_map(&m->a, a, false, g, tma::BOXW, tma::BOXH);
+    if (rc == PB_OK && mode == MODE_P) rc = make_map(&m->b, b, false, g, tma::BOXW, tma::BOXH);
+    if (rc == PB_OK && mode == MODE_U) rc = make_map(&m->x, x, false, g, tma::OWNW, tma::ROWS);
+    if (rc == PB_OK && mode == MODE_U) rc = make_map(&m->z, z, false, g, tma::OWNW, tma::ROWS);
+    if (rc == PB_OK) rc = make_map(&m->code, sys->code, true, g, tma::CODEW, tma::BOXH);
+    return rc;
+}
+
+template <int MODE>
+pb_status tma_prepare() {
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tma::smem_bytes<MODE>());
+        if (e != cudaSuccess) {
+            set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            return PB_ERR_CUDA;
+        }
+        done = true;
+    }
+    return PB_OK;
+}
+
+dim3 tma_grid(const PadGeo &g, int KC) {
+    return dim3((unsigned)cdiv(g.nx - 1, tma::OWNW), (unsigned)cdiv(g.ny - 2, tma::ROWS),
+                (unsigned)cdiv(g.nz - 2, KC));
+}
+
+template <int MODE>
+void tma_launch(const tma::Maps &m, const KArgs<float> &a, const CoefC32 &cp, dim3 grid,
+                cudaStream_t s) {
+    k_stencil_tma<MODE><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(m, a, cp);
+}
+
+// z-chunk length for the TMA kernels (resident blocks from the occupancy API)
+int choose_kc_tma(const PadGeo &g) {
+    static int resident = 0;
+    if (!resident) {
+        int per_sm = 0;
+        if (tma_prepare<MODE_U>() != PB_OK ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<MODE_U>,
+                                                          tma::NTHREADS,
+                                                          tma::smem_bytes<MODE_U>()) != cudaSuccess ||
+            per_sm <= 0) {
+            cudaGetLastError();
+            per_sm = 2;
+        }
+        resident = per_sm * num_sms();
+    }
+    long long cols = (long long)cdiv(g.nx - 1, tma::OWNW) * cdiv(g.ny - 2, tma::ROWS);
+    int best = 8;
+    double best_eff = -1.0;
+    for (int kc = 4; kc <= 64; ++kc) {
+        long long blocks = cols * cdiv(g.nz - 2, kc);
+        double waves = (double)blocks / resident;
+        double eff = waves / ceil(waves) * ((double)kc / (kc + 1.0));
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = kc;
+        }
+    }
+    return best;
+}
+
+struct TmaState {
+    tma::Maps P[2];  // direction kernel, p_old = pa (0) / pb (1)
+    tma::Maps U[2];  // update kernel, p = pb (0) / pa (1)
+};
+
+pb_status build_tma_state(pb_system *sys) {
+    if (sys->tma) return PB_OK;
+    TmaState *t = new (std::nothrow) TmaState();
+    if (!t) return PB_ERR_OOM;
+    pb_status rc = PB_OK;
+    const float *pbuf[2] = {sys->pa32, sys->pb32};
+    for (int c = 0; c < 2 && rc == PB_OK; ++c) {
+        rc = tma_maps(sys, MODE_P, sys->z32, pbuf[c], nullptr, nullptr, &t->P[c]);
+        if (rc == PB_OK) rc = tma_maps(sys, MODE_U, pbuf[c ^ 1], nullptr, sys->d32, sys->z32, &t->U[c]);
+    }
+    if (rc == PB_OK) rc = tma_prepare<MODE_P>();
+    if (rc == PB_OK) rc = tma_prepare<MODE_U>();
+    if (rc != PB_OK) {
+        delete t;
+        return rc;
+    }
+    sys->tma = t;
+    return PB_OK;
+}
+
+// one FP32 PCG iteration (direction + update kernels) with TMA staging;
+// cur selects which of pa/pb holds p_old
+void launch_iter_tma(pb_system *sys, const CoefC32 &cp, int cur, int KC, cudaStream_t s) {
+    TmaState *t = (TmaState *)sys->tma;
+    float *pbuf[2] = {sys->pa32, sys->pb32};
+    KArgs<float> a{};
+    a.code = sys->code;
+    a.st = sys->st;
+    a.partials = sys->partials;
+    a.pg = sys->pad;
+    a.KC = KC;
+    a.out = pbuf[cur ^ 1];
+    dim3 grid = tma_grid(sys->pad, KC);
+    tma_launch<MODE_P>(t->P[cur], a, cp, grid, s);
+    KArgs<float> b = a;
+    b.out = nullptr;
+    b.xv = sys->d32;
+    b.zv = sys->z32;
+    tma_launch<MODE_U>(t->U[cur], b, cp, grid, s);
 }
 
 CoefC32 make_c32(const pb_system *sys) {
@@ -638,7 +845,8 @@ pb_status residual(pb_system *sys, bool fp32_out, cudaStream_t s) {
 // Runs PCG iterations until the device state says done; host polls a pinned
 // copy of the state after every chunk, keeping two chunks in flight.
 template <typename T, class CP>
-pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC, int chunk,
+pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC, int variant,
+                  int chunk,
                   double deadline, cudaStream_t s, int *iters_out) {
     T *bufs[2] = {pa, pb};
     int cur = 0;  // index of p_old
@@ -649,7 +857,14 @@ pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC
     pb_status rc = PB_OK;
     auto issue = [&](int slot) -> pb_status {
         for (int c = 0; c < chunk; ++c) {
-            launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
+            if constexpr (std::is_same<T, float>::value) {
+                if (variant == 1)
+                    launch_iter_tma(sys, cp, cur, KC, s);
+                else
+                    launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
+            } else {
+                launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
+            }
             cur ^= 1;
         }
         note_launch(2 * chunk - 1);
@@ -728,7 +943,104 @@ pb_status init_state(pb_system *sys, double rho, double rr0, double rr_stop, int
     return PB_OK;
 }
 
+// ---------------------------------------------------------------- tuner --
+// Kernel variant (0: register-pipelined warps, 1: TMA-staged, FP32 only)
+// and z-chunk length chosen by timing one PCG iteration of each candidate on
+// the system itself; cached per (precision, grid shape).
+struct Tuning {
+    int variant = 0;
+    int kc = 8;
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, Tuning> g_tune;
+
+pb_status time_candidate(pb_system *sys, int precision, int variant, int kc, cudaStream_t s,
+                         float *ms) {
+    const int reps = 3;
+    cudaEvent_t e0, e1;
+    PB_CUDA_TRY(cudaEventCreate(&e0));
+    PB_CUDA_TRY(cudaEventCreate(&e1));
+    for (int r = 0; r < reps + 1; ++r) {
+        if (r == 1) PB_CUDA_TRY(cudaEventRecord(e0, s));
+        if (precision == PB_MIXED) {
+            CoefC32 cp = make_c32(sys);
+            if (variant == 1)
+                launch_iter_tma(sys, cp, r & 1, kc, s);
+            else
+                launch_iter<float, CoefC32>(sys, cp, sys->z32, (r & 1) ? sys->pb32 : sys->pa32,
+                                            (r & 1) ? sys->pa32 : sys->pb32, sys->d32, sys->z32, kc, s);
+        } else {
+            CoefS64 cp = make_s64(sys);
+            launch_iter<double, CoefS64>(sys, cp, sys->z64, (r & 1) ? sys->pb64 : sys->pa64,
+                                         (r & 1) ? sys->pa64 : sys->pb64, sys->x64, sys->z64, kc, s);
+        }
+        note_launch(2);
+    }
+    PB_CUDA_TRY(cudaEventRecord(e1, s));
+    PB_CUDA_TRY(cudaEventSynchronize(e1));
+    PB_CUDA_TRY(cudaGetLastError());
+    float t = 0.f;
+    PB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / reps;
+    return PB_OK;
+}
+
+pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
+    const PadGeo &g = sys->pad;
+    auto key = std::make_tuple(precision, g.nx, g.ny, g.nz);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *out = it->second;
+            return PB_OK;
+        }
+    }
+    // timing runs use the profile state (never stop); the solver re-initialises
+    // every vector they touch before iterating
+    pb_status rc = init_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1);
+    if (rc != PB_OK) return rc;
+    const int kcs[] = {4, 6, 8, 11, 16, 22, 32, 48};
+    Tuning best;
+    float best_ms = 1e30f;
+    for (int variant = 0; variant < (precision == PB_MIXED ? 2 : 1); ++variant) {
+        for (int kc : kcs) {
+            if (kc > g.nz - 2 && kc != kcs[0]) continue;
+            float ms = 0.f;
+            if ((rc = time_candidate(sys, precision, variant, kc, s, &ms)) != PB_OK) return rc;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.variant = variant;
+                best.kc = kc;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+    }
+    *out = best;
+    return PB_OK;
+}
+
 }  // namespace
+
+pb_status set_tuning(pb_system *sys, int precision, int variant, int kc) {
+    if (kc < 1 || variant < 0 || variant > 1 || (variant == 1 && precision != PB_MIXED)) {
+        set_error("bad tuning (variant %d, z-chunk %d)", variant, kc);
+        return PB_ERR_ARG;
+    }
+    const PadGeo &g = sys->pad;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    Tuning t;
+    t.variant = variant;
+    t.kc = kc;
+    g_tune[std::make_tuple(precision, g.nx, g.ny, g.nz)] = t;
+    return PB_OK;
+}
 
 pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s) {
     const PadGeo &p = sys->pad;
@@ -778,7 +1090,9 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
     const PadGeo &p = sys->pad;
     pb_status rc = ensure_solver_ws(sys, o->precision, s);
     if (rc != PB_OK) return rc;
-    int KC = default_kc(p, o->precision);
+    if (o->precision == PB_MIXED && (rc = build_tma_state(sys)) != PB_OK) return rc;
+    Tuning tune;
+    if ((rc = autotune(sys, o->precision, s, &tune)) != PB_OK) return rc;
     int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
@@ -813,8 +1127,12 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
             PB_CUDA_TRY(cudaMemsetAsync(sys->d32, 0, bytes32, s));
             PB_CUDA_TRY(cudaMemsetAsync(sys->pa32, 0, bytes32, s));
             int it = 0;
-            rc = run_pcg<float, CoefC32>(sys, cp, sys->z32, sys->pa32, sys->pb32, sys->d32, KC, chunk,
-                                         deadline, s, &it);
+            rc = run_pcg<float, CoefC32>(sys, cp, sys->z32, sys->pa32, sys->pb32, sys->d32, tune.kc,
+                                         tune.variant, chunk, deadline, s, &it);
+            if (rc == PB_OK && sys->h_st[0].status == 3) {
+                set_error("a device-side wait reached its limit in the FP32 PCG kernels");
+                return PB_ERR_TIMEOUT;
+            }
             if (rc == PB_ERR_TIMEOUT) {
                 status = PB_ERR_TIMEOUT;
             } else if (rc != PB_OK) {
@@ -859,8 +1177,8 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
                 return rc;
             PB_CUDA_TRY(cudaMemsetAsync(sys->pa64, 0, bytes64, s));
             int it = 0;
-            rc = run_pcg<double, CoefS64>(sys, cp, sys->z64, sys->pa64, sys->pb64, sys->x64, KC,
-                                          chunk, deadline, s, &it);
+            rc = run_pcg<double, CoefS64>(sys, cp, sys->z64, sys->pa64, sys->pb64, sys->x64, tune.kc,
+                                          0, chunk, deadline, s, &it);
             if (rc == PB_ERR_TIMEOUT) status = PB_ERR_TIMEOUT;
             else if (rc != PB_OK) return rc;
             if (rc == PB_OK) iters += it;
@@ -881,6 +1199,7 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
         stats->status = status;
         stats->iters_inner = iters;
         stats->iters_outer = outer;
+        stats->kc = tune.kc + 1000 * tune.variant;
         stats->true_rel_res = fn2 > 0.0 ? sqrt(res2 / fn2) : 0.0;
         stats->seconds = now_s() - t_start;
         stats->dof = (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2);
@@ -892,6 +1211,11 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
     return (pb_status)status;
 }
 
+void free_tma_state(pb_system *sys) {
+    delete (TmaState *)sys->tma;
+    sys->tma = nullptr;
+}
+
 pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cudaStream_t s) {
     if (precision == PB_MIXED && !sys->z32) {
         set_error("no mixed-precision solver state");
@@ -901,11 +1225,38 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
         set_error("no FP64 solver state");
         return PB_ERR_STATE;
     }
-    pb_status rc = init_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1);
-    if (rc != PB_OK) return rc;
-    int KC = default_kc(sys->pad, precision);
+    pb_status rc = PB_OK;
+    if (precision == PB_MIXED && (rc = build_tma_state(sys)) != PB_OK) return rc;
+    Tuning tune;
+    if ((rc = autotune(sys, precision, s, &tune)) != PB_OK) return rc;
+    if ((rc = init_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1)) != PB_OK) return rc;
+    const int KC = tune.kc;
     for (int r = 0; r < reps; ++r) {
-        if (precision == PB_MIXED) {
+        const int cur = r & 1;
+        if (precision == PB_MIXED && tune.variant == 1) {
+            CoefC32 cp = make_c32(sys);
+            TmaState *t = (TmaState *)sys->tma;
+            float *pbuf[2] = {sys->pa32, sys->pb32};
+            dim3 grid = tma_grid(sys->pad, KC);
+            KArgs<float> a{};
+            a.code = sys->code;
+            a.st = sys->st;
+            a.partials = sys->partials;
+            a.pg = sys->pad;
+            a.KC = KC;
+            if (which == 0 || which == 2) {
+                a.out = pbuf[cur ^ 1];
+                tma_launch<MODE_P>(t->P[cur], a, cp, grid, s);
+                PB_LAUNCH_CHECK();
+            }
+            if (which == 1 || which == 2) {
+                a.out = nullptr;
+                a.xv = sys->d32;
+                a.zv = sys->z32;
+                tma_launch<MODE_U>(t->U[cur], a, cp, grid, s);
+                PB_LAUNCH_CHECK();
+            }
+        } else if (precision == PB_MIXED) {
             CoefC32 cp = make_c32(sys);
             dim3 grid = stencil_grid<float>(sys->pad, KC);
             KArgs<float> a{};
@@ -914,15 +1265,16 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
             a.partials = sys->partials;
             a.pg = sys->pad;
             a.KC = KC;
+            float *pbuf[2] = {sys->pa32, sys->pb32};
             if (which == 0 || which == 2) {
                 a.in = sys->z32;
-                a.in2 = (r & 1) ? sys->pb32 : sys->pa32;
-                a.out = (r & 1) ? sys->pa32 : sys->pb32;
+                a.in2 = pbuf[cur];
+                a.out = pbuf[cur ^ 1];
                 k_stencil<float, CoefC32, MODE_P, TYC, MinB<float>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
                 PB_LAUNCH_CHECK();
             }
             if (which == 1 || which == 2) {
-                a.in = (r & 1) ? sys->pa32 : sys->pb32;
+                a.in = pbuf[cur ^ 1];
                 a.in2 = nullptr;
                 a.out = nullptr;
                 a.xv = sys->d32;
@@ -939,15 +1291,16 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
             a.partials = sys->partials;
             a.pg = sys->pad;
             a.KC = KC;
+            double *pbuf[2] = {sys->pa64, sys->pb64};
             if (which == 0 || which == 2) {
                 a.in = sys->z64;
-                a.in2 = (r & 1) ? sys->pb64 : sys->pa64;
-                a.out = (r & 1) ? sys->pa64 : sys->pb64;
+                a.in2 = pbuf[cur];
+                a.out = pbuf[cur ^ 1];
                 k_stencil<double, CoefS64, MODE_P, TYC, MinB<double>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
                 PB_LAUNCH_CHECK();
             }
             if (which == 1 || which == 2) {
-                a.in = (r & 1) ? sys->pa64 : sys->pb64;
+                a.in = pbuf[cur ^ 1];
                 a.in2 = nullptr;
                 a.out = nullptr;
                 a.xv = sys->x64;
@@ -973,14 +1326,17 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
     unsigned blocks = cdiv(g.N, 256);
     if (precision == PB_MIXED) {
         k_canon_to_pad<float><<<blocks, 256, 0, s>>>((const float *)x, (float *)xp, g, p);
+        tma::Maps m;
+        pb_status rc = tma_maps(sys, MODE_A, (const float *)xp, nullptr, nullptr, nullptr, &m);
+        if (rc == PB_OK) rc = tma_prepare<MODE_A>();
+        if (rc != PB_OK) return rc;
+        int KCt = choose_kc_tma(p);
         KArgs<float> a{};
-        a.in = (const float *)xp;
         a.out = (float *)yp;
         a.code = sys->code;
         a.pg = p;
-        a.KC = KC;
-        k_stencil<float, CoefC32, MODE_A, TYC, MinB<float>::v><<<stencil_grid<float>(p, KC), 32 * TYC, 0, s>>>(
-            a, make_c32(sys));
+        a.KC = KCt;
+        tma_launch<MODE_A>(m, a, make_c32(sys), tma_grid(p, KCt), s);
         k_pad_to_canon<float><<<blocks, 256, 0, s>>>((const float *)yp, (float *)y, g, p);
     } else {
         k_canon_to_pad<double><<<blocks, 256, 0, s>>>((const double *)x, (double *)xp, g, p);
