@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--workload", default="globular257", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="VARIANT:ZCHUNK for the FP32 PCG kernels instead of the autotuner "
+                         "(e.g. 1:0 = TMA-staged persistent); for profiler runs")
     return ap.parse_args()
 
 
@@ -246,6 +249,9 @@ def run_ours(args, wl):
     def step(atoms, precision):
         g = pb.pb_build_grid(spec, atoms)
         s = pb.pb_assemble_coeffs(g, params)
+        if args.tuning and precision == pb.MIXED:
+            v, kc = (int(t) for t in args.tuning.split(":"))
+            pb.pb_set_tuning(s, pb.MIXED, v, kc)
         pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
         st = pb.pb_solve(s, pb.SolveOpts(precision=precision, rtol=wl["rtol"]))
         e = pb.pb_energy(s)
@@ -351,7 +357,7 @@ def run_ours(args, wl):
             traffic = json.load(fh).get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": ("k_stencil_tma<MODE_U> (FP32 PCG update, TMA-staged)"
+                "kernel": ("k_stencil_tma<MODE_U> (FP32 PCG update, TMA-staged, persistent)"
                            if stats[-1]["kc"] >= 1000 else
                            "k_stencil<float,CoefC32,MODE_U> (FP32 PCG update)"),
                 "z_chunk": stats[-1]["kc"] % 1000,

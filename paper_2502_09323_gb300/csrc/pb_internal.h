@@ -158,6 +158,7 @@ struct pb_system {
     int solved, have_surface, have_pairs;
     double fnorm2;
     void *tma;          // tensor maps of the FP32 stencil kernels (host object)
+    unsigned int *queue;  // work counters of the TMA stencil kernels (device)
 };
 
 namespace pbg {

@@ -140,6 +140,7 @@ struct KArgs {
     double *partials;
     PadGeo pg;
     int KC;
+    unsigned int *queue;  // TMA kernels: [0] next work item, [1] blocks finished
 };
 
 // block-wide FP64 sum of v (valid in thread 0)
@@ -682,9 +683,21 @@ pb_status tma_prepare() {
     return PB_OK;
 }
 
-dim3 tma_grid(const PadGeo &g, int KC) {
-    return dim3((unsigned)cdiv(g.nx - 1, tma::OWNW), (unsigned)cdiv(g.ny - 2, tma::ROWS),
-                (unsigned)cdiv(g.nz - 2, KC));
+// one block per resident slot (persistent, balanced ranges), at most one
+// block per (tile column, plane) pair
+dim3 tma_grid(const PadGeo &g, int) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (tma_prepare<MODE_U>() != PB_OK ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<MODE_U>,
+                                                          tma::NTHREADS,
+                                                          tma::smem_bytes<MODE_U>()) != cudaSuccess ||
+            per_sm <= 0) {
+            cudaGetLastError();
+            per_sm = 2;
+        }
+    }
+    return dim3((unsigned)std::max(per_sm * num_sms(), 1));
 }
 
 template <int MODE>
@@ -759,6 +772,7 @@ void launch_iter_tma(pb_system *sys, const CoefC32 &cp, int cur, int KC, cudaStr
     a.partials = sys->partials;
     a.pg = sys->pad;
     a.KC = KC;
+    a.queue = sys->queue;
     a.out = pbuf[cur ^ 1];
     dim3 grid = tma_grid(sys->pad, KC);
     tma_launch<MODE_P>(t->P[cur], a, cp, grid, s);
@@ -955,14 +969,12 @@ struct Tuning {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, Tuning> g_tune;
 
+// median of three timings of two PCG iterations (after one warm-up iteration)
 pb_status time_candidate(pb_system *sys, int precision, int variant, int kc, cudaStream_t s,
                          float *ms) {
-    const int reps = 3;
-    cudaEvent_t e0, e1;
-    PB_CUDA_TRY(cudaEventCreate(&e0));
-    PB_CUDA_TRY(cudaEventCreate(&e1));
-    for (int r = 0; r < reps + 1; ++r) {
-        if (r == 1) PB_CUDA_TRY(cudaEventRecord(e0, s));
+    cudaEvent_t ev[7];
+    for (auto &e : ev) PB_CUDA_TRY(cudaEventCreate(&e));
+    auto iter = [&](int r) {
         if (precision == PB_MIXED) {
             CoefC32 cp = make_c32(sys);
             if (variant == 1)
@@ -976,15 +988,22 @@ pb_status time_candidate(pb_system *sys, int precision, int variant, int kc, cud
                                          (r & 1) ? sys->pa64 : sys->pb64, sys->x64, sys->z64, kc, s);
         }
         note_launch(2);
+    };
+    iter(0);
+    int r = 1;
+    for (int m = 0; m < 3; ++m) {
+        PB_CUDA_TRY(cudaEventRecord(ev[2 * m], s));
+        iter(r++);
+        iter(r++);
+        PB_CUDA_TRY(cudaEventRecord(ev[2 * m + 1], s));
     }
-    PB_CUDA_TRY(cudaEventRecord(e1, s));
-    PB_CUDA_TRY(cudaEventSynchronize(e1));
+    PB_CUDA_TRY(cudaEventSynchronize(ev[5]));
     PB_CUDA_TRY(cudaGetLastError());
-    float t = 0.f;
-    PB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    *ms = t / reps;
+    float t[3];
+    for (int m = 0; m < 3; ++m) PB_CUDA_TRY(cudaEventElapsedTime(&t[m], ev[2 * m], ev[2 * m + 1]));
+    for (auto &e : ev) cudaEventDestroy(e);
+    std::sort(t, t + 3);
+    *ms = t[1] / 2.0f;
     return PB_OK;
 }
 
@@ -1003,7 +1022,7 @@ pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
     // every vector they touch before iterating
     pb_status rc = init_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1);
     if (rc != PB_OK) return rc;
-    const int kcs[] = {4, 6, 8, 11, 16, 22, 32, 48};
+    const int kcs[] = {6, 8, 11, 16, 22, 32};
     Tuning best;
     float best_ms = 1e30f;
     for (int variant = 0; variant < (precision == PB_MIXED ? 2 : 1); ++variant) {
@@ -1029,7 +1048,8 @@ pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
 }  // namespace
 
 pb_status set_tuning(pb_system *sys, int precision, int variant, int kc) {
-    if (kc < 1 || variant < 0 || variant > 1 || (variant == 1 && precision != PB_MIXED)) {
+    if (kc < 1 || variant < 0 || variant > 1 ||
+        (variant == 1 && precision != PB_MIXED)) {
         set_error("bad tuning (variant %d, z-chunk %d)", variant, kc);
         return PB_ERR_ARG;
     }
@@ -1042,8 +1062,19 @@ pb_status set_tuning(pb_system *sys, int precision, int variant, int kc) {
     return PB_OK;
 }
 
+// work counters of the TMA stencil kernels ([0] next item, [1] finished
+// blocks); zero between launches because each launch's last block resets them
+pb_status ensure_queue(pb_system *sys, cudaStream_t s) {
+    if (sys->queue) return PB_OK;
+    sys->queue = (unsigned int *)dalloc(4 * sizeof(unsigned int), s);
+    if (!sys->queue) return PB_ERR_OOM;
+    PB_CUDA_TRY(cudaMemsetAsync(sys->queue, 0, 4 * sizeof(unsigned int), s));
+    return PB_OK;
+}
+
 pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s) {
     const PadGeo &p = sys->pad;
+    pb_status rc0 = PB_OK;
     if (!sys->st) {
         sys->st = (CgState *)dalloc(sizeof(CgState), s);
         if (!sys->st) return PB_ERR_OOM;
@@ -1056,6 +1087,7 @@ pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s) {
         sys->npartials = (int)(2 * nb + 64);
         sys->partials = (double *)dalloc(sizeof(double) * sys->npartials, s);
         if (!sys->partials) return PB_ERR_OOM;
+        if ((rc0 = ensure_queue(sys, s)) != PB_OK) return rc0;
     }
     size_t bytes32 = sizeof(float) * (size_t)p.Np, bytes64 = sizeof(double) * (size_t)p.Np;
     if (precision == PB_MIXED && !sys->z32) {
@@ -1244,6 +1276,7 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
             a.partials = sys->partials;
             a.pg = sys->pad;
             a.KC = KC;
+            a.queue = sys->queue;
             if (which == 0 || which == 2) {
                 a.out = pbuf[cur ^ 1];
                 tma_launch<MODE_P>(t->P[cur], a, cp, grid, s);
@@ -1326,16 +1359,18 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
     unsigned blocks = cdiv(g.N, 256);
     if (precision == PB_MIXED) {
         k_canon_to_pad<float><<<blocks, 256, 0, s>>>((const float *)x, (float *)xp, g, p);
+        if (ensure_queue(sys, s) != PB_OK) return PB_ERR_OOM;
         tma::Maps m;
         pb_status rc = tma_maps(sys, MODE_A, (const float *)xp, nullptr, nullptr, nullptr, &m);
         if (rc == PB_OK) rc = tma_prepare<MODE_A>();
         if (rc != PB_OK) return rc;
-        int KCt = choose_kc_tma(p);
+        int KCt = 8;
         KArgs<float> a{};
         a.out = (float *)yp;
         a.code = sys->code;
         a.pg = p;
         a.KC = KCt;
+        a.queue = sys->queue;
         tma_launch<MODE_A>(m, a, make_c32(sys), tma_grid(p, KCt), s);
         k_pad_to_canon<float><<<blocks, 256, 0, s>>>((const float *)yp, (float *)y, g, p);
     } else {
