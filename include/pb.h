@@ -265,6 +265,24 @@ pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int
  * autotuner's choice (which times the candidates on first use of a shape). */
 pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_t z_chunk);
 
+/* pb_apply_dot_noalloc -- y = A x (FP64 operator, interior nodes; boundary
+ * entries of x read as zero, y = 0 on boundary nodes) and *xAx = x.(A x),
+ * computed without allocating any device memory.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory while
+ * they work (an application whose device memory belongs to its own pool or to
+ * another framework, or a latency-critical loop that cannot accept
+ * cudaMalloc's implicit synchronisation).
+ * x, y: device arrays of N doubles in node order; xAx: one device double.
+ * Scratch is a fixed array inside the library (about 128 KB, held by every
+ * GPU that loads the library until the process exits); grids of more than
+ * 16384 * 2048 = 33,554,432 nodes are rejected with PB_ERR_ARG.  The first
+ * call on a device looks up the array's device address (set-up), so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * The system's device must be the current device. */
+pb_status pb_apply_dot_noalloc(const pb_system *s, const double *x, double *y, double *xAx,
+                               void *stream);
+
 /* Number of CUDA kernels launched by this library in this process so far. */
 int64_t pb_kernel_launches(void);
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "pb_profile_kernels": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P]),
     "pb_kernel_launches": (C.c_int64, []),
     "pb_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
+    "pb_apply_dot_noalloc": (C.c_int, [P, P, P, P, P]),
     "pb_last_error": (C.c_char_p, []),
     "pb_version": (C.c_char_p, []),
 }
