@@ -526,12 +526,32 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
     }
     pb_status rc = check_opts(opts);
     if (rc != PB_OK) return rc;
-    pb_status worst = PB_OK;
     for (int i = 0; i < n; ++i) {
         if (!systems[i]) {
             set_error("pb_solve_batch: system %d is NULL", i);
             return PB_ERR_ARG;
         }
+        if (systems[i]->g->device != systems[0]->g->device) {
+            set_error("pb_solve_batch: systems live on different devices");
+            return PB_ERR_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (systems[j] == systems[i]) {
+                set_error("pb_solve_batch: system %d appears twice", i);
+                return PB_ERR_ARG;
+            }
+    }
+    if (n == 0) return PB_OK;
+    DeviceGuard dg(systems[0]->g->device);
+    if (opts->precision == PB_MIXED) {
+        pb_status r = solve_batch(systems, n, opts, (cudaStream_t)stream, stats);
+        if (r == PB_ERR_NOCONV) set_error("a system stopped before reaching rtol");
+        if (r == PB_ERR_TIMEOUT) set_error("the batch exceeded its time budget");
+        return r;
+    }
+    // FP64: one plain PCG after the other
+    pb_status worst = PB_OK;
+    for (int i = 0; i < n; ++i) {
         pb_status r = pb_solve(systems[i], opts, nullptr, stream, &stats[i]);
         if (r == PB_ERR_CUDA || r == PB_ERR_OOM) return r;
         if (r != PB_OK) worst = r;
@@ -567,3 +587,4 @@ pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_
 }
 
 }  // extern "C"
+

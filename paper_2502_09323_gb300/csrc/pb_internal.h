@@ -183,6 +183,8 @@ pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s);
 pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cudaStream_t s);
 void free_tma_state(pb_system *sys);
 pb_status set_tuning(pb_system *sys, int precision, int variant, int kc);
+pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, cudaStream_t s,
+                      pb_solve_stats *stats);
 
 // ------------------------------------------------------------- energy.cu --
 pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);

@@ -1,11 +1,15 @@
 // FP32 PCG stencil kernels with TMA staging (included by solve.cu).
 //
-// Blocks are resident for the whole launch (one per resident slot) and pull
-// work items -- z-chunks of KC planes of one 128 x 8 tile column -- from a
-// global atomic counter.  The producer announces each chunk in a small
-// descriptor ring before arming the chunk's first plane, so consumers learn
-// it through the same mbarrier; the TMA pipeline keeps streaming across
-// chunks.  One producer warp (lane 0) issues, for every plane, tensor-map
+// One launch serves every system of a table (a single solve is a table of
+// one; a batch of uneven solves is a table of many).  Blocks are resident for
+// the whole launch and pull work items -- z-chunks of KC planes of one
+// 128 x 8 tile column of one system -- from a global atomic counter.  The
+// producer announces each chunk in a small descriptor ring before arming the
+// chunk's first plane, so consumers learn it through the same mbarrier; the
+// TMA pipeline keeps streaming across chunks and systems.  Each item's dot
+// products go to that item's own slot; the block that finishes a system's
+// last item sums the system's slots in item order and updates its CG state,
+// so every result is independent of scheduling and of the other systems.  One producer warp (lane 0) issues, for every plane, tensor-map
 // (cp.async.bulk.tensor) loads of
 //   * the streamed vector on a 136 x 10 box (4 columns of x halo on each side
 //     and one halo row above and below; out-of-range elements are zero),
@@ -80,6 +84,23 @@ struct Maps {
     CUtensorMap code;   // 160 x 10 box of code bytes
 };
 
+// One system of a launch table (device memory).
+struct SysEntry {  // aligned as CUtensorMap
+    Maps P[2];          // direction kernel, p_old = pa (parity 0) / pb (1)
+    Maps U[2];          // update kernel, p = pb (parity 0) / pa (1)
+    Maps A;             // apply
+    PadGeo pg;
+    CoefC32 cp;
+    float *pbuf[2];     // pa, pb
+    float *x, *z;       // solution increment, preconditioned residual
+    float *y;           // apply output
+    CgState *st;
+    double *partials;   // per (item, warp) slot q = li*ROWS + w: sigma at [q],
+                        // rho and rr at [nitems*ROWS + 2q], [.. + 1]
+    unsigned int *cnt;  // items finished in the current launch
+    int xtiles, ytiles, nchunk, KC, nitems, item_base;
+};
+
 // ------------------------------------------------------------------- PTX --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -124,38 +145,29 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 
 }  // namespace tma
 
-// MODE_P / MODE_U / MODE_A on the compressed FP32 operator.
+// MODE_P / MODE_U / MODE_A on the compressed FP32 operator, over every
+// system of tab (item_base ascending; total_items = sum of nitems).
 template <int MODE>
 __global__ void __launch_bounds__(tma::NTHREADS, 2)
-k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp) {
+k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, int cur,
+              unsigned int *queue) {
     using namespace tma;
     using L = SlotLayout<MODE>;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ double sred[NTHREADS / 32];
     __shared__ int s_abort;
+    __shared__ int s_desc[NSLOT][6];  // i0, j0, kfirst, len, system, local item
 
-    float alpha = 0.f, beta = 0.f;
-    if (MODE != MODE_A) {
-        if (A.st->done) return;
-        if (MODE == MODE_P) beta = (float)A.st->beta;
-        if (MODE == MODE_U) alpha = (float)A.st->alpha;
-    }
-    const PadGeo g = A.pg;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // work items: (tile column, z-chunk), chunks of one column consecutive
-    const int xtiles = (g.nx - 1 + OWNW - 1) / OWNW;
-    const int ytiles = (g.ny - 2 + ROWS - 1) / ROWS;
-    const int nzi = g.nz - 2;
-    const int nchunk = (nzi + A.KC - 1) / A.KC;
-    const int nitems = xtiles * ytiles * nchunk;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NSLOT * L::stride);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
-    // descriptor ring (at most NSLOT chunks can be in flight)
-    __shared__ int4 s_desc[NSLOT];
-
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSLOT; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -166,20 +178,6 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
     }
     __syncthreads();
 
-    struct Seg {
-        int i0, j0, kfirst, len;
-    };
-    auto decode = [&](int item) {
-        Seg sg;
-        const int col = item / nchunk, c = item - col * nchunk;
-        sg.kfirst = 1 + c * A.KC;
-        sg.len = min(A.KC, nzi - c * A.KC);
-        sg.i0 = (col % xtiles) * OWNW;
-        sg.j0 = 1 + (col / xtiles) * ROWS;
-        return sg;
-    };
-
-    float acc0 = 0.f, acc1 = 0.f;
     if (w == ROWS) {
         // ------------------------------------------------------- producer
         if (lane == 0) {
@@ -187,10 +185,29 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
             for (int s = 0; s < NSLOT; ++s) last_use[s] = -1;
             int gt = 0, nseg = 0;  // running plane and chunk counters
             for (;;) {
-                const int item = (int)atomicAdd(A.queue, 1u);
-                const bool end = item >= nitems;
-                const Seg sg = end ? Seg{0, 0, 0, -1} : decode(item);
-                const int nplanes = end ? 1 : sg.len + 2;
+                const int item = (int)atomicAdd(queue, 1u);
+                const bool end = item >= total_items;
+                int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1;
+                const SysEntry *e = tab;
+                if (!end) {
+                    int lo = 0, hi = nsys - 1;  // last entry with item_base <= item
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (tab[mid].item_base <= item) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    sys = lo;
+                    e = tab + sys;
+                    if (MODE != MODE_A && *(volatile int *)&e->st->done) continue;  // converged
+                    li = item - e->item_base;
+                    const int col = li / e->nchunk, c = li - col * e->nchunk;
+                    kfirst = 1 + c * e->KC;
+                    len = min(e->KC, e->pg.nz - 2 - c * e->KC);
+                    i0 = (col % e->xtiles) * OWNW;
+                    j0 = 1 + (col / e->xtiles) * ROWS;
+                }
+                const Maps *m = MODE == MODE_P ? &e->P[cur] : (MODE == MODE_U ? &e->U[cur] : &e->A);
+                const int nplanes = end ? 1 : len + 2;
                 bool stop = false;
                 for (int t = 0; t < nplanes; ++t, ++gt) {
                     const int s = gt % NSLOT, u = gt / NSLOT;
@@ -204,22 +221,30 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
                         break;
                     }
                     const uint32_t bar = full0 + 8 * s;
-                    if (t == 0) s_desc[nseg % NSLOT] = make_int4(sg.i0, sg.j0, sg.kfirst, sg.len);
+                    if (t == 0) {
+                        int *d = s_desc[nseg % NSLOT];
+                        d[0] = i0;
+                        d[1] = j0;
+                        d[2] = kfirst;
+                        d[3] = len;
+                        d[4] = sys;
+                        d[5] = li;
+                    }
                     if (end) {
                         mbar_arrive(bar);  // no data: announces the end
                         last_use[s] = -1;
                         break;
                     }
                     const uint32_t slot = smem_u32(smem + s * L::stride);
-                    const int kp = sg.kfirst - 1 + t;
+                    const int kp = kfirst - 1 + t;
                     mbar_expect_tx(bar, L::tx);
-                    tma_load3(slot + L::a, &maps.a, sg.i0 - 4, sg.j0 - 1, kp, bar);
-                    if (MODE == MODE_P) tma_load3(slot + L::b, &maps.b, sg.i0 - 4, sg.j0 - 1, kp, bar);
-                    if (MODE == MODE_U) {
-                        tma_load3(slot + L::x, &maps.x, sg.i0, sg.j0, kp, bar);
-                        tma_load3(slot + L::z, &maps.z, sg.i0, sg.j0, kp, bar);
+                    tma_load3(slot + L::a, &m->a, i0 - 4, j0 - 1, kp, bar);
+                    if constexpr (MODE == MODE_P) tma_load3(slot + L::b, &m->b, i0 - 4, j0 - 1, kp, bar);
+                    if constexpr (MODE == MODE_U) {
+                        tma_load3(slot + L::x, &m->x, i0, j0, kp, bar);
+                        tma_load3(slot + L::z, &m->z, i0, j0, kp, bar);
                     }
-                    tma_load3(slot + L::code, &maps.code, sg.i0 - 16, sg.j0 - 1, kp, bar);
+                    tma_load3(slot + L::code, &m->code, i0 - 16, j0 - 1, kp, bar);
                     last_use[s] = u;
                 }
                 ++nseg;
@@ -232,9 +257,6 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
     } else {
         // ------------------------------------------------------- consumers
         const int r = w + 1;  // this row inside the halo boxes
-        const float dg_in = 6.f * cp.w_in, dg_out = 6.f * cp.w_out + cp.kap;
-        const float dinv_in = 1.f / dg_in, dinv_out = 1.f / dg_out;
-
         auto slot_ptr = [&](int t) { return smem + (t % NSLOT) * L::stride; };
         auto wait_full = [&](int t) -> bool {
             if (!mbar_wait(full0 + 8 * (t % NSLOT), (t / NSLOT) & 1)) {
@@ -247,6 +269,7 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8 * (t % NSLOT));
         };
+        float beta = 0.f;
         // streamed value (P: z + beta p_old) of box row rr
         auto val4 = [&](const uint8_t *sl, int rr, float (&v)[4]) {
             const float *a = reinterpret_cast<const float *>(sl + L::a) + rr * BOXW + 4 + lane * 4;
@@ -274,27 +297,36 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
         };
 
         int gt = 0, nseg = 0;
-        bool ok = true;
         for (;; ++nseg) {
             // the chunk's first plane's barrier also publishes its descriptor
-            if (!wait_full(gt)) {
-                ok = false;
-                break;
-            }
-            const int4 d = s_desc[nseg % NSLOT];
-            if (d.w < 0) break;  // end of work
-            const Seg sg{d.x, d.y, d.z, d.w};
-            const int j = sg.j0 + w;
-            const int ib = sg.i0 + lane * 4;
+            if (!wait_full(gt)) break;
+            const int *d = s_desc[nseg % NSLOT];
+            const int len = d[3];
+            if (len < 0) break;  // end of work
+            const int i0 = d[0], j0 = d[1], kfirst = d[2], sys = d[4], li = d[5];
+            const SysEntry *e = tab + sys;
+            const PadGeo g = e->pg;
+            const CoefC32 cp = e->cp;
+            float alpha = 0.f;
+            if (MODE == MODE_P) beta = (float)e->st->beta;
+            if (MODE == MODE_U) alpha = (float)e->st->alpha;
+            const float dg_in = 6.f * cp.w_in, dg_out = 6.f * cp.w_out + cp.kap;
+            const float dinv_in = 1.f / dg_in, dinv_out = 1.f / dg_out;
+            float *const outp = MODE == MODE_P ? e->pbuf[cur ^ 1] : (MODE == MODE_A ? e->y : nullptr);
+            float *const xg = e->x, *const zg = e->z;
+            const int j = j0 + w;
+            const int ib = i0 + lane * 4;
             const bool active = j <= g.ny - 2;
             const bool grp_ok = active && ib < g.sx;
             const int gt0 = gt;
+            float acc0 = 0.f, acc1 = 0.f;
             float pm[4], pc[4], pn[4];
             uint32_t cm = 0, cc = 0, cn = 0;
             // +z weights of this row at plane k-1 (the -z weights of plane k).
             // A plane on the fast path has no listed +z edge, so its pure +z
-            // weights are exact too; only a segment's first plane loads them.
+            // weights are exact too; only a chunk's first plane loads them.
             float wzc[4] = {0.f, 0.f, 0.f, 0.f};
+            bool ok = true;
             {
                 const uint8_t *s0 = slot_ptr(gt0);
                 val4(s0, r, pm);
@@ -307,8 +339,8 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
                 val4(s1, r, pc);
                 cc = code4(s1, r);
             }
-            for (int t = 1; ok && t <= sg.len; ++t) {
-                const int k = sg.kfirst + t - 1;
+            for (int t = 1; ok && t <= len; ++t) {
+                const int k = kfirst + t - 1;
                 if (!wait_full(gt0 + t + 1)) {
                     ok = false;
                     break;
@@ -463,13 +495,13 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
                 release(gt0 + t);
                 if (grp_ok) {
                     if (MODE == MODE_P)
-                        *reinterpret_cast<float4 *>(A.out + base + ib) = make_float4(pc[0], pc[1], pc[2], pc[3]);
+                        *reinterpret_cast<float4 *>(outp + base + ib) = make_float4(pc[0], pc[1], pc[2], pc[3]);
                     if (MODE == MODE_U) {
-                        *reinterpret_cast<float4 *>(A.xv + base + ib) = make_float4(xv[0], xv[1], xv[2], xv[3]);
-                        *reinterpret_cast<float4 *>(A.zv + base + ib) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+                        *reinterpret_cast<float4 *>(xg + base + ib) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+                        *reinterpret_cast<float4 *>(zg + base + ib) = make_float4(zv[0], zv[1], zv[2], zv[3]);
                     }
                     if (MODE == MODE_A)
-                        *reinterpret_cast<float4 *>(A.out + base + ib) = make_float4(y[0], y[1], y[2], y[3]);
+                        *reinterpret_cast<float4 *>(outp + base + ib) = make_float4(y[0], y[1], y[2], y[3]);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -480,74 +512,96 @@ k_stencil_tma(const __grid_constant__ tma::Maps maps, KArgs<float> A, CoefC32 cp
                 cc = cn;
             }
             if (!ok) break;
-            release(gt0 + sg.len + 1);  // the chunk's last plane (+z halo only)
-            gt = gt0 + sg.len + 2;
+            release(gt0 + len + 1);  // the chunk's last plane (+z halo only)
+            gt = gt0 + len + 2;
+            if (MODE == MODE_A) continue;
+
+            // ---- this warp's dot products of this item -> their own slot;
+            // the warp that fills a system's last slot sums all slots in a
+            // fixed order and updates that system's CG state (no barriers)
+            const double b0 = warp_sum_d((double)acc0), b1 = warp_sum_d((double)acc1);
+            const int nslots = e->nitems * ROWS;
+            unsigned last = 0;
+            if (lane == 0) {
+                const int idx = li * ROWS + w;
+                if (MODE == MODE_P) {
+                    e->partials[idx] = b0;
+                } else {
+                    e->partials[nslots + 2 * idx] = b0;
+                    e->partials[nslots + 2 * idx + 1] = b1;
+                }
+                __threadfence();
+                last = atomicAdd(e->cnt, 1u) == (unsigned)nslots - 1;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                double t0 = 0.0, t1 = 0.0;
+                for (int q = lane; q < nslots; q += 32) {
+                    if (MODE == MODE_P) {
+                        t0 += __ldcg(e->partials + q);
+                    } else {
+                        t0 += __ldcg(e->partials + nslots + 2 * q);
+                        t1 += __ldcg(e->partials + nslots + 2 * q + 1);
+                    }
+                }
+                t0 = warp_sum_d(t0);
+                t1 = warp_sum_d(t1);
+                if (lane == 0) {
+                    CgState *st = e->st;
+                    if (MODE == MODE_P) {
+                        st->sigma = t0;
+                        if (st->status == 3) {
+                            st->done = 1;
+                        } else if (st->profile) {
+                            st->alpha = isfinite(t0) && t0 != 0.0 ? st->rho / t0 : 0.0;
+                        } else if (!(t0 > 0.0) || !isfinite(t0)) {
+                            st->done = 1;
+                            st->status = 1;
+                        } else {
+                            st->alpha = st->rho / t0;
+                        }
+                    } else {
+                        st->beta = t0 / st->rho;
+                        st->rho = t0;
+                        st->rr = t1;
+                        st->iter += 1;
+                        if (st->status == 3) {
+                            st->done = 1;
+                        } else if (st->profile) {
+                            // timing run: keep going
+                        } else if (!isfinite(t1)) {
+                            st->done = 1;
+                            st->status = 1;
+                        } else if (t1 <= st->rr_stop) {
+                            st->done = 1;
+                            st->status = 0;
+                        } else if (st->iter >= st->max_iter) {
+                            st->done = 1;
+                            st->status = 2;
+                        }
+                    }
+                    *e->cnt = 0u;
+                    __threadfence();
+                }
+            }
         }
     }
     __syncthreads();
+    // a device-side wait gave up: stop every system of the table
+    if (s_abort && threadIdx.x == 0 && MODE != MODE_A) {
+        for (int q = 0; q < nsys; ++q) {
+            atomicExch(&tab[q].st->status, 3);
+            atomicExch(&tab[q].st->done, 1);
+        }
+    }
     // the last block to leave resets the work counter for the next launch
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(A.queue + 1, 1u) == gridDim.x - 1) {
-            A.queue[0] = 0u;
-            A.queue[1] = 0u;
+        if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+            queue[0] = 0u;
+            queue[1] = 0u;
             __threadfence();
-        }
-    }
-    if (s_abort) {
-        if (threadIdx.x == 0 && MODE != MODE_A) {
-            atomicExch(&A.st->status, 3);
-            atomicExch(&A.st->done, 1);
-        }
-        if (MODE == MODE_A) return;
-    }
-    if (MODE == MODE_A) return;
-
-    const int nb = gridDim.x * gridDim.y * gridDim.z;
-    double t0, t1;
-    if (MODE == MODE_P) {
-        if (last_block_total<NTHREADS, false>(A.st, A.partials, nb, (double)acc0, 0.0, sred, t0, t1)) {
-            if (threadIdx.x == 0) {
-                CgState *s = A.st;
-                s->sigma = t0;
-                if (s->status == 3) {
-                    s->done = 1;
-                } else if (s->profile) {
-                    s->alpha = isfinite(t0) && t0 != 0.0 ? s->rho / t0 : 0.0;
-                } else if (!(t0 > 0.0) || !isfinite(t0)) {
-                    s->done = 1;
-                    s->status = 1;
-                } else {
-                    s->alpha = s->rho / t0;
-                }
-                s->counter = 0;
-            }
-        }
-    } else {
-        if (last_block_total<NTHREADS, true>(A.st, A.partials, nb, (double)acc0, (double)acc1, sred,
-                                             t0, t1)) {
-            if (threadIdx.x == 0) {
-                CgState *s = A.st;
-                s->beta = t0 / s->rho;
-                s->rho = t0;
-                s->rr = t1;
-                s->iter += 1;
-                if (s->status == 3) {
-                    s->done = 1;
-                } else if (s->profile) {
-                    // timing run: keep going
-                } else if (!isfinite(t1)) {
-                    s->done = 1;
-                    s->status = 1;
-                } else if (t1 <= s->rr_stop) {
-                    s->done = 1;
-                    s->status = 0;
-                } else if (s->iter >= s->max_iter) {
-                    s->done = 1;
-                    s->status = 2;
-                }
-                s->counter = 0;
-            }
         }
     }
 }
