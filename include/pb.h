@@ -250,6 +250,60 @@ pb_status pb_apply(pb_system *s, int32_t precision, const void *x, void *y, void
 pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_opts *opts,
                          void *stream, pb_solve_stats *stats);
 
+/* ---------------------------------------------------------------------
+ * Continuous-batching engine.  A serving loop submits assembled systems
+ * (pb_assemble_coeffs, and pb_coulomb_terms when energies are wanted) as
+ * they arrive; the engine keeps up to `capacity` of them resident in one
+ * launch table that a pump thread replays as a CUDA graph of mixed-precision
+ * PCG iterations (Sec. 3.2's solve with FP32 inner iterations and FP64
+ * iterative refinement).  A system submitted while others run joins at the
+ * next replay once a slot is free; a finished one leaves at once and is
+ * reported through pb_engine_wait.  The paper solves one system at a time:
+ * the engine is the serving form of the same solve, and a system's result is
+ * the same (bit for bit, for the same z-chunk) alone or in any mix.
+ * ------------------------------------------------------------------- */
+typedef struct pb_engine pb_engine;
+
+typedef struct {
+    int64_t ticket;          /* from pb_engine_submit */
+    pb_system *system;       /* the submitted system (its phi holds the solution) */
+    pb_solve_stats stats;    /* status PB_OK, PB_ERR_NOCONV, PB_ERR_TIMEOUT, or the
+                                engine's error; seconds = time since admission */
+    double t_submit, t_admit, t_done;  /* CLOCK_MONOTONIC seconds */
+} pb_engine_result;
+
+/* pb_engine_create -- engine on `device` with `capacity` slots (1..4096);
+ * opts->rtol / inner_rtol / max_iter / max_outer apply to every solve
+ * (precision and time_budget_s are ignored: the engine is mixed precision).
+ * Allocates a small device table (about 3.5 KB per slot) and starts the
+ * pump thread. */
+pb_status pb_engine_create(int32_t device, int32_t capacity, const pb_solve_opts *opts,
+                           pb_engine **out);
+
+/* pb_engine_submit -- queue s for solving.  `stream` is the stream on which
+ * s was assembled (its work is waited for on the device, not on the host);
+ * the solver workspace is allocated here, on that stream.  From submission
+ * until its result is returned by pb_engine_wait the system belongs to the
+ * engine: do not use or free it.  PB_ERR_ARG if s is already in the engine
+ * or lives on another device. */
+pb_status pb_engine_submit(pb_engine *e, pb_system *s, void *stream, int64_t *ticket);
+
+/* pb_engine_wait -- move up to max_out finished solves into out (*n_out of
+ * them), waiting up to timeout_s seconds for at least one (0: do not wait).
+ * Returns the engine's error if it failed and nothing is left to report. */
+pb_status pb_engine_wait(pb_engine *e, double timeout_s, pb_engine_result *out, int32_t max_out,
+                         int32_t *n_out);
+
+/* pb_engine_query -- systems waiting for a slot, systems in the table, and
+ * graph replays so far (any pointer may be NULL); returns the engine's
+ * error status. */
+pb_status pb_engine_query(pb_engine *e, int32_t *n_pending, int32_t *n_active, int64_t *replays);
+
+/* pb_engine_destroy -- stop the pump thread after the replays in flight and
+ * free the engine.  Systems still waiting or running are handed back
+ * unsolved (their results, with PB_ERR_STATE, are dropped). */
+pb_status pb_engine_destroy(pb_engine *e);
+
 /* pb_profile_kernels -- timing hook: run `reps` launches of the PCG kernels
  * of the given precision on s's solver state with the convergence test off
  * (iterate and state are overwritten, so call it after pb_energy).  which:

@@ -29,7 +29,7 @@ __all__ = [
     "pb_build_grid", "pb_assemble_coeffs", "pb_coulomb_terms", "pb_solve", "pb_energy",
     "pb_get_array", "pb_get_phi", "pb_apply", "pb_solve_batch", "pb_last_error",
     "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning",
-    "solve_molecule", "library_path", "loaded", "PBError",
+    "solve_molecule", "library_path", "loaded", "PBError", "Engine",
 ]
 
 _alloc_lock = threading.Lock()
@@ -316,6 +316,72 @@ def pb_solve_batch(systems, opts: SolveOpts, stream=None) -> list:
     stats = (N.SolveStatsC * n)()
     N.check(N.lib().pb_solve_batch(arr, n, C.byref(opts.c()), _stream(stream), stats))
     return [N.struct_dict(s) for s in stats]
+
+
+class Engine:
+    """Owns a ``pb_engine*``: continuous batching of mixed-precision solves.
+
+    ``submit`` hands an assembled :class:`System` to the engine (it joins the
+    running launch table as soon as a slot is free); ``wait`` returns finished
+    solves as dicts with ``ticket``, ``system`` (the submitted object),
+    ``stats`` and the engine's monotonic timestamps ``t_submit``,
+    ``t_admit``, ``t_done``.  A submitted system must not be used until it
+    has been returned by ``wait``.
+    """
+
+    def __init__(self, capacity: int = 64, opts: SolveOpts | None = None, device: int | None = None):
+        use_torch_allocator()
+        if device is None:
+            device = _torch().cuda.current_device()
+        h = C.c_void_p()
+        o = (opts or SolveOpts()).c()
+        N.check(N.lib().pb_engine_create(int(device), int(capacity), C.byref(o), C.byref(h)))
+        self._h = h
+        self.capacity = int(capacity)
+        self._systems: dict[int, System] = {}
+        self._lock = threading.Lock()
+
+    def submit(self, system: System, stream=None) -> int:
+        t = C.c_int64()
+        with self._lock:
+            N.check(N.lib().pb_engine_submit(self._h, system.handle, _stream(stream), C.byref(t)))
+            self._systems[int(t.value)] = system
+        return int(t.value)
+
+    def wait(self, timeout_s: float = 0.0, max_out: int = 256) -> list:
+        out = (N.EngineResultC * max_out)()
+        n = C.c_int32()
+        N.check(N.lib().pb_engine_wait(self._h, float(timeout_s), out, int(max_out), C.byref(n)))
+        res = []
+        with self._lock:
+            for r in out[: n.value]:
+                res.append({"ticket": int(r.ticket), "system": self._systems.pop(int(r.ticket), None),
+                            "stats": N.struct_dict(r.stats), "t_submit": r.t_submit,
+                            "t_admit": r.t_admit, "t_done": r.t_done})
+        return res
+
+    def query(self) -> dict:
+        p, a, r = C.c_int32(), C.c_int32(), C.c_int64()
+        rc = N.lib().pb_engine_query(self._h, C.byref(p), C.byref(a), C.byref(r))
+        return {"pending": p.value, "active": a.value, "replays": r.value, "rc": rc}
+
+    def close(self) -> None:
+        if self._h:
+            N.check(N.lib().pb_engine_destroy(self._h))
+            self._h = None
+            self._systems.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 def pb_profile_kernels(system: System, precision: int, which: int, reps: int, stream=None) -> None:

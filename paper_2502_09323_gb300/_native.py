@@ -58,6 +58,11 @@ class GridInfoC(C.Structure):
                 ("n_flux", C.c_int64), ("n_inside", C.c_int64)]
 
 
+class EngineResultC(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("system", C.c_void_p), ("stats", SolveStatsC),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -81,6 +86,11 @@ SIGNATURES = {
     "pb_kernel_launches": (C.c_int64, []),
     "pb_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "pb_apply_dot_noalloc": (C.c_int, [P, P, P, P, P]),
+    "pb_engine_create": (C.c_int, [C.c_int32, C.c_int32, P, P]),
+    "pb_engine_submit": (C.c_int, [P, P, P, P]),
+    "pb_engine_wait": (C.c_int, [P, C.c_double, P, C.c_int32, P]),
+    "pb_engine_query": (C.c_int, [P, P, P, P]),
+    "pb_engine_destroy": (C.c_int, [P]),
     "pb_last_error": (C.c_char_p, []),
     "pb_version": (C.c_char_p, []),
 }

@@ -559,6 +559,75 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
     return worst;
 }
 
+pb_status pb_engine_create(int32_t device, int32_t capacity, const pb_solve_opts *opts,
+                           pb_engine **out) {
+    set_error("");
+    if (!out || capacity < 1 || capacity > 4096) {
+        set_error("pb_engine_create: NULL output or capacity outside 1..4096");
+        return PB_ERR_ARG;
+    }
+    *out = nullptr;
+    if (opts) {
+        pb_status rc = check_opts(opts);
+        if (rc != PB_OK) return rc;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("pb_engine_create: no CUDA device %d", device);
+        return PB_ERR_ARG;
+    }
+    DeviceGuard dg(device);
+    return engine_create(device, capacity, opts, out);
+}
+
+pb_status pb_engine_submit(pb_engine *e, pb_system *s, void *stream, int64_t *ticket) {
+    set_error("");
+    if (!e || !s || !ticket) {
+        set_error("pb_engine_submit: NULL argument");
+        return PB_ERR_ARG;
+    }
+    DeviceGuard dg(s->g->device);
+    long long t = 0;
+    pb_status rc = engine_submit(e, s, (cudaStream_t)stream, &t);
+    *ticket = t;
+    return rc;
+}
+
+pb_status pb_engine_wait(pb_engine *e, double timeout_s, pb_engine_result *out, int32_t max_out,
+                         int32_t *n_out) {
+    set_error("");
+    if (!e || !n_out || max_out < 0 || (max_out > 0 && !out) || !(timeout_s >= 0.0)) {
+        set_error("pb_engine_wait: bad argument");
+        return PB_ERR_ARG;
+    }
+    int n = 0;
+    pb_status rc = engine_wait(e, timeout_s, out, max_out, &n);
+    *n_out = n;
+    return rc;
+}
+
+pb_status pb_engine_query(pb_engine *e, int32_t *n_pending, int32_t *n_active, int64_t *replays) {
+    set_error("");
+    if (!e) {
+        set_error("pb_engine_query: NULL engine");
+        return PB_ERR_ARG;
+    }
+    int p = 0, a = 0;
+    long long r = 0;
+    pb_status rc = engine_query(e, &p, &a, &r);
+    if (n_pending) *n_pending = p;
+    if (n_active) *n_active = a;
+    if (replays) *replays = r;
+    return rc;
+}
+
+pb_status pb_engine_destroy(pb_engine *e) {
+    set_error("");
+    if (!e) return PB_OK;
+    return engine_destroy(e);
+}
+
 pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int32_t reps,
                              void *stream) {
     set_error("");

@@ -118,6 +118,8 @@ struct CgState {
     int status;      // 0 ok, 1 breakdown, 2 max_iter
     unsigned int counter;  // last-block counter of the reductions
     int profile;     // 1 = timing run: never stop
+    int cur;         // FP32 TMA kernels: which of pa/pb holds p_old (flips per iteration)
+    int pad;
 };
 
 struct EnergyAcc {
@@ -185,6 +187,11 @@ void free_tma_state(pb_system *sys);
 pb_status set_tuning(pb_system *sys, int precision, int variant, int kc);
 pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, cudaStream_t s,
                       pb_solve_stats *stats);
+pb_status engine_create(int device, int capacity, const pb_solve_opts *o, pb_engine **out);
+pb_status engine_submit(pb_engine *e, pb_system *sys, cudaStream_t s, long long *ticket);
+pb_status engine_wait(pb_engine *e, double timeout_s, pb_engine_result *out, int max_out, int *n_out);
+pb_status engine_query(pb_engine *e, int *n_pending, int *n_active, long long *replays);
+pb_status engine_destroy(pb_engine *e);
 
 // ------------------------------------------------------------- energy.cu --
 pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);

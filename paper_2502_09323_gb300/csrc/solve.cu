@@ -28,9 +28,13 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <tuple>
 #include <vector>
 #include <type_traits>
@@ -701,10 +705,10 @@ dim3 tma_grid(const PadGeo &g, int) {
 }
 
 template <int MODE>
-void tma_launch(const tma::SysEntry *dev_tab, int nsys, int total_items, int cur,
-                unsigned int *queue, dim3 grid, cudaStream_t s) {
+void tma_launch(const tma::SysEntry *dev_tab, int nsys, int total_items, unsigned int *queue,
+                dim3 grid, cudaStream_t s) {
     k_stencil_tma<MODE><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(dev_tab, nsys,
-                                                                           total_items, cur, queue);
+                                                                           total_items, queue);
 }
 
 struct TmaState {
@@ -796,8 +800,8 @@ void launch_iter_tma(pb_system *sys, const CoefC32 &, int cur, int KC, cudaStrea
     TmaState *t = (TmaState *)sys->tma;
     if (tma_use_kc(sys, KC, s) != PB_OK) return;
     dim3 grid = tma_grid(sys->pad, KC);
-    tma_launch<MODE_P>(t->dev, 1, t->host.nitems, cur, sys->queue, grid, s);
-    tma_launch<MODE_U>(t->dev, 1, t->host.nitems, cur, sys->queue, grid, s);
+    tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
+    tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
 }
 
 CoefC32 make_c32(const pb_system *sys) {
@@ -1299,11 +1303,11 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
             if ((rc = tma_use_kc(sys, KC, s)) != PB_OK) return rc;
             dim3 grid = tma_grid(sys->pad, KC);
             if (which == 0 || which == 2) {
-                tma_launch<MODE_P>(t->dev, 1, t->host.nitems, cur, sys->queue, grid, s);
+                tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
                 PB_LAUNCH_CHECK();
             }
             if (which == 1 || which == 2) {
-                tma_launch<MODE_U>(t->dev, 1, t->host.nitems, cur, sys->queue, grid, s);
+                tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
                 PB_LAUNCH_CHECK();
             }
         } else if (precision == PB_MIXED) {
@@ -1403,7 +1407,7 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
             set_error("apply table upload: %s", cudaGetErrorString(ce));
             return PB_ERR_CUDA;
         }
-        tma_launch<MODE_A>(de, 1, nitems, 0, sys->queue, tma_grid(p, 8), s);
+        tma_launch<MODE_A>(de, 1, nitems, sys->queue, tma_grid(p, 8), s);
         PB_LAUNCH_CHECK();
         dfree(de, s);
         k_pad_to_canon<float><<<blocks, 256, 0, s>>>((const float *)yp, (float *)y, g, p);
@@ -1443,7 +1447,7 @@ pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, 
     const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     const double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
     const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
-    const int chunk = 8;  // even: the p ping-pong parity is 0 at every replay start
+    const int chunk = 8;  // PCG iterations per graph replay
     pb_status rc = PB_OK;
 
     std::vector<int> kc(n);
@@ -1536,8 +1540,8 @@ pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, 
             break;
         }
         for (int c = 0; c < chunk; ++c) {
-            tma_launch<MODE_P>(dtab, n, total, c & 1, queue, grid, cs);
-            tma_launch<MODE_U>(dtab, n, total, c & 1, queue, grid, cs);
+            tma_launch<MODE_P>(dtab, n, total, queue, grid, cs);
+            tma_launch<MODE_U>(dtab, n, total, queue, grid, cs);
         }
         if (cudaStreamEndCapture(cs, &graph) != cudaSuccess ||
             cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
@@ -1715,5 +1719,7 @@ pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, 
         if (status[i] != PB_OK) worst = (pb_status)status[i];
     return worst;
 }
+
+#include "engine.cuh"
 
 }  // namespace pbg

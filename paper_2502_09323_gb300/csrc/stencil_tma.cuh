@@ -154,16 +154,19 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }  // namespace tma
 
 // MODE_P / MODE_U / MODE_A on the compressed FP32 operator, over every
-// system of tab (item_base ascending; total_items = sum of nitems).
+// system of tab (item_base ascending; total_items = sum of nitems).  With
+// nsys < 0 the table size and item total are read from queue[2] and
+// queue[3], so a captured launch follows a table that changes between
+// replays.
 template <int MODE>
 __global__ void __launch_bounds__(tma::NTHREADS, 2)
-k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, int cur,
+k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
               unsigned int *queue) {
     using namespace tma;
     using L = SlotLayout<MODE>;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_abort;
-    __shared__ int s_desc[NSLOT][6];  // i0, j0, kfirst, len, system, local item
+    __shared__ int s_abort, s_nsys, s_total;
+    __shared__ int s_desc[NSLOT][7];  // i0, j0, kfirst, len, system, local item, parity
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NSLOT * L::stride);
@@ -175,8 +178,12 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, 
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
+        s_nsys = nsys < 0 ? (int)((volatile unsigned int *)queue)[2] : nsys;
+        s_total = nsys < 0 ? (int)((volatile unsigned int *)queue)[3] : total_items;
     }
     __syncthreads();
+    nsys = s_nsys;
+    total_items = s_total;
 
     if (w == ROWS) {
         // ------------------------------------------------------- producer
@@ -187,7 +194,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, 
             for (;;) {
                 const int item = (int)atomicAdd(queue, 1u);
                 const bool end = item >= total_items;
-                int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1;
+                int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1, cur = 0;
                 const SysEntry *e = tab;
                 if (!end) {
                     int lo = 0, hi = nsys - 1;  // last entry with item_base <= item
@@ -199,6 +206,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, 
                     sys = lo;
                     e = tab + sys;
                     if (MODE != MODE_A && *(volatile int *)&e->st->done) continue;  // converged
+                    if (MODE != MODE_A) cur = *(volatile int *)&e->st->cur;
                     li = item - e->item_base;
                     const int col = li / e->nchunk, c = li - col * e->nchunk;
                     kfirst = 1 + c * e->KC;
@@ -229,6 +237,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, 
                         d[3] = len;
                         d[4] = sys;
                         d[5] = li;
+                        d[6] = cur;
                     }
                     if (end) {
                         mbar_arrive(bar);  // no data: announces the end
@@ -303,7 +312,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, 
             const int *d = s_desc[nseg % NSLOT];
             const int len = d[3];
             if (len < 0) break;  // end of work
-            const int i0 = d[0], j0 = d[1], kfirst = d[2], sys = d[4], li = d[5];
+            const int i0 = d[0], j0 = d[1], kfirst = d[2], sys = d[4], li = d[5], cur = d[6];
             const SysEntry *e = tab + sys;
             const PadGeo g = e->pg;
             const CoefC32 cp = e->cp;
@@ -566,6 +575,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items, 
                         st->rho = t0;
                         st->rr = t1;
                         st->iter += 1;
+                        st->cur ^= 1;  // the new p_old is this iteration's p
                         if (st->status == 3) {
                             st->done = 1;
                         } else if (st->profile) {

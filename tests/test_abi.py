@@ -56,7 +56,7 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2502_09323_gb300 import _native as N
     structs = {"pb_grid_spec": N.GridSpecC, "pb_params": N.ParamsC, "pb_solve_opts": N.SolveOptsC,
                "pb_solve_stats": N.SolveStatsC, "pb_energy_terms": N.EnergyC,
-               "pb_grid_info": N.GridInfoC}
+               "pb_grid_info": N.GridInfoC, "pb_engine_result": N.EngineResultC}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
