@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--workload", default="globular257", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=6.0)
     ap.add_argument("--tuning", default=None,
                     help="VARIANT:ZCHUNK for the FP32 PCG kernels instead of the autotuner "
                          "(e.g. 1:0 = TMA-staged persistent); for profiler runs")
@@ -217,6 +222,140 @@ def config_obj(args, wl):
             "l2": "inputs larger than L2 (working set ~1 GB per solve)"}
 
 
+# ------------------------------------------------------------ batched --
+BATCH_SIZES = (65, 97, 129, 161, 193)
+
+
+def run_batched(args, pb, pb_inputs, torch):
+    """256 uneven molecules (atom counts log-uniform in [200, 3000], molecule
+    i seeded 4000 + i), uniform grids of spacing 0.5 A, solved to 1e-8 by
+    one graph-launched batch; beside them the same systems solved one at a
+    time by plain FP64 Jacobi-PCG."""
+    from paper_2502_09323_gb300 import serving
+    count = args.batch_count
+    mols = pb_inputs.batch_molecules(count, 4000, 200, 3000)
+    specs = [serving.uniform_spec(a, h=0.5, fill=1.5, sizes=BATCH_SIZES) for a in mols]
+    params = pb.Params()
+    systems = []
+    for a, sp in zip(mols, specs):
+        g = pb.pb_build_grid(sp, a)
+        s = pb.pb_assemble_coeffs(g, params)
+        pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+        systems.append(s)
+    mixed = pb.SolveOpts(precision=pb.MIXED, rtol=1e-8)
+    fp64 = pb.SolveOpts(precision=pb.FP64, rtol=1e-8)
+    # warm-up: tune every grid shape once (both precisions)
+    first = {}
+    for i, sp in enumerate(specs):
+        first.setdefault(sp.n, i)
+    warm = [systems[i] for i in first.values()]
+    pb.pb_solve_batch(warm, mixed)
+    for s in warm:
+        pb.pb_solve(s, fp64)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st = pb.pb_solve_batch(systems, mixed)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_mixed = a.elapsed_time(b) / 1e3
+    e_mixed = [pb.pb_energy(s)["e_total"] for s in systems[:8]]
+    a.record(stream)
+    st64 = [pb.pb_solve(s, fp64) for s in systems]
+    b.record(stream)
+    torch.cuda.synchronize()
+    t64 = a.elapsed_time(b) / 1e3
+    e64 = [pb.pb_energy(s)["e_total"] for s in systems[:8]]
+    dof = [x["dof"] for x in st]
+    iters = [x["iters_inner"] for x in st]
+    shapes = {}
+    for sp in specs:
+        shapes[sp.n[0]] = shapes.get(sp.n[0], 0) + 1
+    out = {
+        "workload": f"{count} globular molecules, atoms log-uniform [200, 3000] (seed 4000 + i), "
+                    f"uniform grids h = 0.5 A, n in {list(BATCH_SIZES)}, fill 1.5, eps 2/80, "
+                    "0.145 M, zero BC, rtol 1e-8",
+        "grids": {str(k): v for k, v in sorted(shapes.items())},
+        "solves_per_s": count / t_mixed, "seconds": t_mixed,
+        "fp64_plain_solves_per_s": count / t64, "fp64_seconds": t64,
+        "speedup_mixed_over_fp64": t64 / t_mixed,
+        "dof_total": int(sum(dof)),
+        "dof_iter_per_s": sum(d * i for d, i in zip(dof, iters)) / t_mixed,
+        "iters_inner_mean": statistics.mean(iters),
+        "true_rel_res_max": max(x["true_rel_res"] for x in st),
+        "fp64_true_rel_res_max": max(x["true_rel_res"] for x in st64),
+        "all_converged": all(x["status"] == 0 for x in st) and all(x["status"] == 0 for x in st64),
+        "energy_rel_diff_mixed_vs_fp64_max": max(abs(m - f) / abs(f) for m, f in zip(e_mixed, e64)),
+    }
+    del systems
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------------ serving --
+def run_serving(args, pb, pb_inputs, torch):
+    """Poisson stream of solves (atom counts log-uniform in [300, 50000],
+    arrivals and counts seeded 5000, molecule j seeded 5000 + j) served with
+    continuous batching under a 150 GB device-memory budget; uniform grids of
+    spacing 0.5 A stand in for the 0.25 A octree."""
+    from paper_2502_09323_gb300 import serving
+    count = args.serve_requests
+    sizes = pb_inputs.batch_sizes(count, 5000, 300, 50000)
+    arrivals = pb_inputs.poisson_arrivals(count, args.serve_rate, seed=5000)
+    reqs = [serving.Request(rid=j, atoms=pb_inputs.globular_molecule(int(n), seed=5000 + j),
+                            arrival_s=float(t)) for j, (n, t) in enumerate(zip(sizes, arrivals))]
+    opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-8)
+    # warm-up: the autotuner sees every grid shape of the stream once
+    shapes = sorted({serving.uniform_spec(r.atoms, h=0.5).n[0] for r in reqs})
+    with pb.Engine(capacity=4, opts=opts) as eng:
+        for n in shapes:
+            one = pb_inputs.globular_molecule(40, seed=n)
+            g = pb.pb_build_grid(pb.GridSpec(n=(n, n, n), origin=(-0.25 * (n - 1),) * 3, h=0.5),
+                                 one)
+            s = pb.pb_assemble_coeffs(g, pb.Params())
+            eng.submit(s)
+            while not eng.wait(timeout_s=0.1):
+                pass
+            del s, g
+    torch.cuda.synchronize()
+    launches0 = pb.pb_kernel_launches()
+    with serving.Server(capacity=64, hbm_budget_bytes=150e9, opts=opts, h=0.5) as srv:
+        recs = srv.run(reqs)
+        max_used = srv.max_used
+    launches = pb.pb_kernel_launches() - launches0
+    summ = serving.latency_summary(recs)
+    # one small request again with plain FP64 on the GPU: energy difference
+    small = min(reqs, key=lambda r: len(r.atoms))
+    g = pb.pb_build_grid(small.spec, small.atoms)
+    s = pb.pb_assemble_coeffs(g, pb.Params())
+    pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+    pb.pb_solve(s, pb.SolveOpts(precision=pb.FP64, rtol=1e-10))
+    e64 = pb.pb_energy(s)["e_total"]
+    em = next(r for r in recs if r["rid"] == small.rid)["energy"]["e_total"]
+    dofs = [r["stats"]["dof"] for r in recs]
+    out = {
+        "workload": f"{count} requests, Poisson arrivals at {args.serve_rate:g}/s (seed 5000), "
+                    "globular molecules with atoms log-uniform [300, 50000], uniform grids "
+                    "h = 0.5 A (32k+1 nodes per axis, fill 1.5) standing in for the 0.25 A octree, "
+                    "mixed precision to 1e-8, 150 GB budget, 64 slots",
+        "rate_hz": args.serve_rate, **summ,
+        "engine_mean_ms": 1e3 * statistics.mean(r["engine_s"] for r in recs),
+        "max_budget_used_gb": max_used / 1e9,
+        "grid_sizes": sorted({r["n"] for r in recs}),
+        "dof_total": int(sum(dofs)),
+        "all_converged": all(r["stats"]["status"] == 0 for r in recs),
+        "true_rel_res_max": max(r["stats"]["true_rel_res"] for r in recs),
+        "energy_rel_diff_vs_fp64_gpu": abs(em - e64) / abs(e64),
+        "gpu_launches": int(launches),
+    }
+    del s, g
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ ours --
 def run_ours(args, wl):
     import numpy as np
@@ -371,6 +510,9 @@ def run_ours(args, wl):
         smp = oracle_sample(wl, fp64["iters"] if fp64 else None)
         cpu = cpu_baseline_obj(smp)
 
+    batched = None if args.no_batched else run_batched(args, pb, pb_inputs, torch)
+    serving_line = None if args.no_serving else run_serving(args, pb, pb_inputs, torch)
+
     lat_ms = sorted(1e3 * v for v in lat)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -391,6 +533,8 @@ def run_ours(args, wl):
                        "p99": lat_ms[min(len(lat_ms) - 1, math.ceil(0.99 * len(lat_ms)) - 1)]},
         "fp64_plain": fp64,
         "energy_kT": energy,
+        "batched": batched,
+        "serving": serving_line,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -210,9 +210,11 @@ void pb_system_free(pb_system *s);
 
 /* pb_coulomb_terms -- analytic N-body sums of Sec. 3.3: PB_CT_SURFACE
  * computes Phi_e and Psi_e at the crossing points of flux edges; PB_CT_PAIRS
- * the Coulomb energy; PB_CT_BOUNDARY recomputes the boundary values.  FP32
- * tiled kernel with split (hi+lo) coordinates and compensated sums, FP64
- * results, kept on the device inside s. */
+ * the Coulomb energy (both: FP32 tiled kernel with split (hi+lo)
+ * coordinates and compensated sums, FP64 results); PB_CT_BOUNDARY recomputes
+ * the Coulomb / Debye-Hueckel boundary values of Sec. 2.3 (FP64 kernel, so
+ * that the Dirichlet lift carries no FP32 rounding).  Results stay on the
+ * device inside s. */
 pb_status pb_coulomb_terms(pb_system *s, int32_t which, void *stream);
 
 /* pb_solve -- Jacobi-preconditioned CG for (G^T W G + C) phi = f (the
@@ -255,8 +257,8 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
  * (pb_assemble_coeffs, and pb_coulomb_terms when energies are wanted) as
  * they arrive; the engine keeps up to `capacity` of them resident in one
  * launch table that a pump thread replays as a CUDA graph of mixed-precision
- * PCG iterations (Sec. 3.2's solve with FP32 inner iterations and FP64
- * iterative refinement).  A system submitted while others run joins at the
+ * PCG iterations (the CG solve of Eq. matrixequation, Sec. 4, with FP32
+ * inner iterations and FP64 iterative refinement).  A system submitted while others run joins at the
  * next replay once a slot is free; a finished one leaves at once and is
  * reported through pb_engine_wait.  The paper solves one system at a time:
  * the engine is the serving form of the same solve, and a system's result is

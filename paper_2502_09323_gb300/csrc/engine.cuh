@@ -6,7 +6,8 @@
 // kernels) of every system in the table; a system that is submitted while
 // others are running takes a free slot and joins at the next replay, and a
 // finished one leaves its slot at once.  The FP64 iterative refinement of
-// Sec. 3.2's solve runs per system between its inner solves: the host sees an
+// the CG solve of Eq. matrixequation (Sec. 3.1; CG as in Sec. 4) runs per
+// system between its inner solves: the host sees an
 // inner solve end in the state mirror copied back after every replay and
 // queues that system's promotion, true residual and refinement step, whose
 // decision (next inner tolerance, convergence, stagnation, iteration limits)

@@ -990,41 +990,42 @@ struct Tuning {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, Tuning> g_tune;
 
-// median of three timings of two PCG iterations (after one warm-up iteration)
+// one PCG iteration of the given kernel variant and z-chunk (timing runs)
+void tune_iter(pb_system *sys, int precision, int variant, int kc, int r, cudaStream_t s) {
+    if (precision == PB_MIXED) {
+        CoefC32 cp = make_c32(sys);
+        if (variant == 1)
+            launch_iter_tma(sys, cp, r & 1, kc, s);
+        else
+            launch_iter<float, CoefC32>(sys, cp, sys->z32, (r & 1) ? sys->pb32 : sys->pa32,
+                                        (r & 1) ? sys->pa32 : sys->pb32, sys->d32, sys->z32, kc, s);
+    } else {
+        CoefS64 cp = make_s64(sys);
+        launch_iter<double, CoefS64>(sys, cp, sys->z64, (r & 1) ? sys->pb64 : sys->pa64,
+                                     (r & 1) ? sys->pa64 : sys->pb64, sys->x64, sys->z64, kc, s);
+    }
+    note_launch(2);
+}
+
+// time of two PCG iterations with z-chunk kc (after one untimed iteration,
+// which also absorbs the switch of the launch-table entry to kc)
 pb_status time_candidate(pb_system *sys, int precision, int variant, int kc, cudaStream_t s,
                          float *ms) {
-    cudaEvent_t ev[7];
-    for (auto &e : ev) PB_CUDA_TRY(cudaEventCreate(&e));
-    auto iter = [&](int r) {
-        if (precision == PB_MIXED) {
-            CoefC32 cp = make_c32(sys);
-            if (variant == 1)
-                launch_iter_tma(sys, cp, r & 1, kc, s);
-            else
-                launch_iter<float, CoefC32>(sys, cp, sys->z32, (r & 1) ? sys->pb32 : sys->pa32,
-                                            (r & 1) ? sys->pa32 : sys->pb32, sys->d32, sys->z32, kc, s);
-        } else {
-            CoefS64 cp = make_s64(sys);
-            launch_iter<double, CoefS64>(sys, cp, sys->z64, (r & 1) ? sys->pb64 : sys->pa64,
-                                         (r & 1) ? sys->pa64 : sys->pb64, sys->x64, sys->z64, kc, s);
-        }
-        note_launch(2);
-    };
-    iter(0);
-    int r = 1;
-    for (int m = 0; m < 3; ++m) {
-        PB_CUDA_TRY(cudaEventRecord(ev[2 * m], s));
-        iter(r++);
-        iter(r++);
-        PB_CUDA_TRY(cudaEventRecord(ev[2 * m + 1], s));
-    }
-    PB_CUDA_TRY(cudaEventSynchronize(ev[5]));
+    cudaEvent_t ev[2];
+    PB_CUDA_TRY(cudaEventCreate(&ev[0]));
+    PB_CUDA_TRY(cudaEventCreate(&ev[1]));
+    tune_iter(sys, precision, variant, kc, 0, s);
+    PB_CUDA_TRY(cudaEventRecord(ev[0], s));
+    tune_iter(sys, precision, variant, kc, 1, s);
+    tune_iter(sys, precision, variant, kc, 2, s);
+    PB_CUDA_TRY(cudaEventRecord(ev[1], s));
+    PB_CUDA_TRY(cudaEventSynchronize(ev[1]));
     PB_CUDA_TRY(cudaGetLastError());
-    float t[3];
-    for (int m = 0; m < 3; ++m) PB_CUDA_TRY(cudaEventElapsedTime(&t[m], ev[2 * m], ev[2 * m + 1]));
-    for (auto &e : ev) cudaEventDestroy(e);
-    std::sort(t, t + 3);
-    *ms = t[1] / 2.0f;
+    float t = 0.f;
+    PB_CUDA_TRY(cudaEventElapsedTime(&t, ev[0], ev[1]));
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    *ms = t / 2.0f;
     return PB_OK;
 }
 
@@ -1043,26 +1044,43 @@ pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
     // every vector they touch before iterating
     pb_status rc = init_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1);
     if (rc != PB_OK) return rc;
-    const int kcs[] = {8, 6, 11, 16, 22, 32};  // first = default
-    Tuning best;
-    best.variant = precision == PB_MIXED ? 1 : 0;
-    float best_ms = 1e30f;
     // mixed precision always runs the TMA-staged kernels (the batched solver
     // shares them, so a system gives the same bits alone and in a batch);
     // only their z-chunk is tuned.  FP64 runs the register-pipelined kernels.
-    {
-        const int variant = precision == PB_MIXED ? 1 : 0;
-        for (int kc : kcs) {
-            if (kc > g.nz - 2 && kc != kcs[0]) continue;
+    const int variant = precision == PB_MIXED ? 1 : 0;
+    Tuning best;
+    best.variant = variant;
+    const int kcs[] = {8, 6, 11, 16, 22, 32};  // first = default
+    // a persistent launch balances its work queue only with a few items per
+    // block: longer chunks that leave fewer are not candidates
+    const long long blocks = variant == 1 ? (long long)tma_grid(g, 8).x : 0;
+    const long long floor_items = variant == 1 ? std::min<long long>(tma_items(g, kcs[0]), 4 * blocks) : 0;
+    std::vector<int> cand;
+    for (int kc : kcs) {
+        if (kc != kcs[0] && kc > g.nz - 2) continue;
+        if (variant == 1 && kc != kcs[0] && tma_items(g, kc) < floor_items) continue;
+        cand.push_back(kc);
+    }
+    // clocks and caches to steady state, then round-robin timings (drift
+    // during tuning then affects every candidate alike); median per candidate
+    for (int i = 0; i < 12; ++i) tune_iter(sys, precision, variant, kcs[0], i, s);
+    const int rounds = 3;
+    std::vector<std::vector<float>> t(cand.size());
+    for (int r = 0; r < rounds; ++r)
+        for (size_t c = 0; c < cand.size(); ++c) {
             float ms = 0.f;
-            if ((rc = time_candidate(sys, precision, variant, kc, s, &ms)) != PB_OK) return rc;
-            // a candidate must beat the incumbent by 3% (timing noise would
-            // otherwise make the choice, and the dot-product partition, vary)
-            if (ms < 0.97f * best_ms) {
-                best_ms = ms;
-                best.variant = variant;
-                best.kc = kc;
-            }
+            if ((rc = time_candidate(sys, precision, variant, cand[c], s, &ms)) != PB_OK) return rc;
+            t[c].push_back(ms);
+        }
+    float best_ms = 1e30f;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        std::sort(t[c].begin(), t[c].end());
+        const float ms = t[c][rounds / 2];
+        // a candidate must beat the incumbent by 3% (timing noise would
+        // otherwise make the choice, and the dot-product partition, vary)
+        if (ms < 0.97f * best_ms) {
+            best_ms = ms;
+            best.kc = cand[c];
         }
     }
     {
