@@ -88,8 +88,19 @@ pb_status pb_set_allocator(pb_alloc_fn alloc, pb_free_fn release, void *ctx);
  * on the device (Sec. 2.3 "perfil", Sec. 3.4): a cube of side fill * extent
  * (extent = largest axis span of the union of [x_i - R_i, x_i + R_i])
  * centred on the atoms' bounding box, h = side / (max n - 1), n[0]==n[1]==n[2]
- * required.  Octree fields are reserved (kind PB_GRID_OCTREE returns
- * PB_ERR_UNIMPL). */
+ * required.
+ *
+ * Octree grid (kind PB_GRID_OCTREE; Sec. 3 and Sec. 3.4 refinement near the
+ * molecular surface, 2:1-balanced 8^3-cell bricks with hanging-node
+ * constraints): cell sizes h_bulk / 2^l down to h_fine (h_bulk must be
+ * h_fine times a power of two, at most 2^7).  A brick is split where its
+ * box lies within refine_dist of an atom sphere surface; refine_dist must
+ * be at least the largest radius, h_fine and 1.5 h_bulk.  If n[0] > 0 the
+ * domain is n[0]^3 coarse bricks of side 8 h_bulk from `origin`; otherwise
+ * n[0] = ceil(fill * extent / (8 h_bulk)) bricks centred on the atoms'
+ * bounding box.  Node arrays of an octree use the slot layout: brick b (in
+ * Morton order) owns slots 512 b + (8k + j) 8 + i, its low-corner nodes;
+ * N = 512 * bricks.  Listed-edge ids are d * N + slot of the low end. */
 typedef struct {
     int32_t kind;
     int32_t n[3];
@@ -157,11 +168,14 @@ typedef struct {
     int32_t n[3];
     double origin[3];
     double h;
-    int64_t n_nodes;          /* nx*ny*nz                                  */
+    int64_t n_nodes;          /* N: nx*ny*nz (uniform) or 512*n_bricks      */
     int64_t n_atoms;
     int64_t n_cross;          /* listed edges (see PB_ARR_CROSS_ID)        */
     int64_t n_flux;           /* listed edges whose endpoints differ       */
     int64_t n_inside;         /* solute nodes                              */
+    int32_t kind;             /* PB_GRID_UNIFORM or PB_GRID_OCTREE          */
+    int32_t n_levels;         /* octree: levels (1 + log2(h_bulk/h_fine))   */
+    int64_t n_bricks;         /* octree: leaf bricks (N = 512 n_bricks)     */
 } pb_grid_info;
 
 /* Arrays that pb_get_array copies out (element type, length). */
@@ -186,6 +200,11 @@ enum {
     PB_ARR_PHI,          /* double [N] solution incl. boundary values        */
     PB_ARR_PHI_SURF,     /* double [n_cross] Phi_e (0 on non-flux edges)     */
     PB_ARR_PSI_SURF,     /* double [n_cross] Psi_e (0 on non-flux edges)     */
+    PB_ARR_OCT_BRICKS,   /* int32  [4*n_bricks] octree: low corner (x, y, z in
+                            units of h_fine) and level of each brick           */
+    PB_ARR_OCT_KIND,     /* uint8  [N] octree: 0 unknown with a 7-point row, 1
+                            boundary, 2 hanging, 3 unknown next to a level
+                            change (explicit row)                           */
     PB_ARR_COUNT
 };
 

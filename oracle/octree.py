@@ -36,9 +36,10 @@ following reading, which the GPU library implements independently:
   sum_l kappa(h_l) * (cells_l / 8)), and A = P^T K P over the regular
   interior nodes, P the hanging-node interpolation.  On a single-level tree
   this is exactly the uniform operator (G^T W G + C).
-* refine_dist must be at least the largest radius and h_fine, so that every
-  solute node, every edge meeting the surface and every charge cell lies in
-  the all-finest region, where everything matches the uniform grid at h_fine.
+* refine_dist must be at least the largest radius, h_fine and 1.5 h_bulk, so
+  that every solute node, every edge meeting the surface and every charge
+  cell lies in the all-finest region (where everything matches the uniform
+  grid at h_fine), and every row next to a level change sees solvent only.
 """
 from __future__ import annotations
 
@@ -148,8 +149,8 @@ def build(atoms, h_fine: float, h_bulk: float, refine_dist: float, fill: float =
     Lmax = int(round(math.log2(ratio)))
     if Lmax < 0 or h_fine * (1 << Lmax) != h_bulk:
         raise ValueError("h_bulk must be h_fine times a power of two")
-    if refine_dist < max(float(atoms[:, 3].max()), h_fine):
-        raise ValueError("refine_dist must be at least the largest radius and h_fine")
+    if refine_dist < max(float(atoms[:, 3].max()), h_fine, 1.5 * h_bulk):
+        raise ValueError("refine_dist must be at least the largest radius, h_fine and 1.5 h_bulk")
     if origin is None:
         origin, n0 = place(atoms, h_bulk, fill)
     origin = np.asarray(origin, dtype=np.float64)

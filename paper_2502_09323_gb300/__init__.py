@@ -25,7 +25,7 @@ from ._native import (BC_COULOMB, BC_DH, BC_ZERO, CT_ALL, CT_BOUNDARY, CT_PAIRS,
                       CT_SURFACE, DEVICE, FP64, HOST, MIXED, PBError)
 
 __all__ = [
-    "GridSpec", "Params", "SolveOpts", "Grid", "System",
+    "GridSpec", "OctreeSpec", "Params", "SolveOpts", "Grid", "System",
     "pb_build_grid", "pb_assemble_coeffs", "pb_coulomb_terms", "pb_solve", "pb_energy",
     "pb_get_array", "pb_get_phi", "pb_apply", "pb_solve_batch", "pb_last_error",
     "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning",
@@ -102,13 +102,36 @@ class GridSpec:
 
     def c(self) -> N.GridSpecC:
         s = N.GridSpecC()
-        s.kind = 0
+        s.kind = N.GRID_UNIFORM
         n = self.n if not isinstance(self.n, int) else (self.n,) * 3
         for d in range(3):
             s.n[d] = int(n[d])
             s.origin[d] = float(self.origin[d])
         s.h = float(self.h)
         s.fill = float(self.fill)
+        return s
+
+
+@dataclasses.dataclass
+class OctreeSpec:
+    """Octree brick grid: cells h_bulk / 2^l down to h_fine, refined within
+    refine_dist of the atom spheres.  n0 = 0 places n0^3 coarse bricks
+    automatically (cube of fill x extent); n0 > 0 uses ``origin``."""
+    h_fine: float = 0.25
+    h_bulk: float = 1.0
+    refine_dist: float = 3.0
+    fill: float = 1.5
+    n0: int = 0
+    origin: tuple = (0.0, 0.0, 0.0)
+
+    def c(self) -> N.GridSpecC:
+        s = N.GridSpecC()
+        s.kind = N.GRID_OCTREE
+        s.n[0] = int(self.n0)
+        for d in range(3):
+            s.origin[d] = float(self.origin[d])
+        s.fill = float(self.fill)
+        s.h_fine, s.h_bulk, s.refine_dist = float(self.h_fine), float(self.h_bulk), float(self.refine_dist)
         return s
 
 
@@ -274,6 +297,8 @@ _ARRAYS = {
     "phi": (N.ARR_PHI, np.float64, "N"),
     "phi_surf": (N.ARR_PHI_SURF, np.float64, "nc"),
     "psi_surf": (N.ARR_PSI_SURF, np.float64, "nc"),
+    "oct_bricks": (N.ARR_OCT_BRICKS, np.int32, "nb4"),
+    "oct_kind": (N.ARR_OCT_KIND, np.uint8, "N"),
 }
 
 
@@ -285,12 +310,17 @@ def pb_get_array(obj, name: str, stream=None) -> np.ndarray:
     else:
         g, s = obj, None
     info = N.grid_info(g.handle)
-    cnt = {"N": info.n_nodes, "nc": info.n_cross, "nc3": 3 * info.n_cross}[kind]
+    cnt = {"N": info.n_nodes, "nc": info.n_cross, "nc3": 3 * info.n_cross,
+           "nb4": 4 * info.n_bricks}[kind]
     out = np.empty(max(int(cnt), 1), dtype=dt)
     N.check(N.lib().pb_get_array(g.handle, s.handle if s else None, which,
                                  out.ctypes.data_as(C.c_void_p), out.nbytes, HOST, _stream(stream)))
     out = out[:cnt]
-    return out.reshape(-1, 3) if kind == "nc3" else out
+    if kind == "nc3":
+        return out.reshape(-1, 3)
+    if kind == "nb4":
+        return out.reshape(-1, 4)
+    return out
 
 
 def pb_get_phi(system: System, stream=None) -> np.ndarray:

@@ -16,7 +16,9 @@ FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 CT_BOUNDARY, CT_SURFACE, CT_PAIRS, CT_ALL = 1, 2, 4, 7
 (ARR_INSIDE, ARR_CROSS_ID, ARR_CROSS_ALPHA, ARR_CROSS_RP, ARR_CROSS_SIGN, ARR_WX, ARR_WY, ARR_WZ,
- ARR_KAPPA, ARR_DIAG, ARR_RHS, ARR_BC, ARR_PHI, ARR_PHI_SURF, ARR_PSI_SURF) = range(15)
+ ARR_KAPPA, ARR_DIAG, ARR_RHS, ARR_BC, ARR_PHI, ARR_PHI_SURF, ARR_PSI_SURF, ARR_OCT_BRICKS,
+ ARR_OCT_KIND) = range(17)
+GRID_UNIFORM, GRID_OCTREE = 0, 1
 
 
 class PBError(RuntimeError):
@@ -55,7 +57,8 @@ class EnergyC(C.Structure):
 class GridInfoC(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("origin", C.c_double * 3), ("h", C.c_double),
                 ("n_nodes", C.c_int64), ("n_atoms", C.c_int64), ("n_cross", C.c_int64),
-                ("n_flux", C.c_int64), ("n_inside", C.c_int64)]
+                ("n_flux", C.c_int64), ("n_inside", C.c_int64), ("kind", C.c_int32),
+                ("n_levels", C.c_int32), ("n_bricks", C.c_int64)]
 
 
 class EngineResultC(C.Structure):

@@ -150,6 +150,7 @@ void pb_grid_free(pb_grid *g) {
     dfree(g->csign, s);
     dfree(g->rowstart, s);
     dfree(g->d_info, s);
+    if (g->is_oct) oct_grid_free(g, s);
     cudaStreamSynchronize(s);
     delete g;
 }
@@ -162,20 +163,37 @@ pb_status pb_build_grid(const pb_grid_spec *spec, const double *atoms, int64_t n
         return PB_ERR_ARG;
     }
     *out = nullptr;
-    if (spec->kind == PB_GRID_OCTREE) {
-        set_error("octree grids are not available in this build");
-        return PB_ERR_UNIMPL;
-    }
-    if (spec->kind != PB_GRID_UNIFORM) {
+    const bool oct = spec->kind == PB_GRID_OCTREE;
+    if (spec->kind != PB_GRID_UNIFORM && !oct) {
         set_error("unknown grid kind %d", spec->kind);
         return PB_ERR_ARG;
     }
-    for (int d = 0; d < 3; ++d)
+    if (oct) {
+        if (!(spec->h_fine > 0.0) || !(spec->h_bulk >= spec->h_fine) || !isfinite(spec->h_bulk) ||
+            !(spec->refine_dist >= 0.0) || !isfinite(spec->refine_dist)) {
+            set_error("octree: need 0 < h_fine <= h_bulk and refine_dist >= 0");
+            return PB_ERR_ARG;
+        }
+        if (spec->n[0] < 0 || spec->n[0] > 1024) {
+            set_error("octree: n[0] (coarse bricks per axis) out of range [0, 1024]");
+            return PB_ERR_ARG;
+        }
+        if (spec->n[0] == 0 && (!(spec->fill > 1.0) || !isfinite(spec->fill))) {
+            set_error("automatic placement needs fill > 1");
+            return PB_ERR_ARG;
+        }
+        for (int d = 0; d < 3; ++d)
+            if (spec->n[0] > 0 && !isfinite(spec->origin[d])) {
+                set_error("grid origin is not finite");
+                return PB_ERR_ARG;
+            }
+    }
+    for (int d = 0; d < 3 && !oct; ++d)
         if (spec->n[d] < 3 || spec->n[d] > 4096) {
             set_error("grid size n[%d]=%d out of range [3, 4096]", d, spec->n[d]);
             return PB_ERR_ARG;
         }
-    if ((long long)spec->n[0] * spec->n[1] * spec->n[2] > (1ll << 31) - 1) {
+    if (!oct && (long long)spec->n[0] * spec->n[1] * spec->n[2] > (1ll << 31) - 1) {
         set_error("grid has more than 2^31 nodes");
         return PB_ERR_ARG;
     }
@@ -183,7 +201,9 @@ pb_status pb_build_grid(const pb_grid_spec *spec, const double *atoms, int64_t n
         set_error("grid spacing h must be >= 0 and finite");
         return PB_ERR_ARG;
     }
-    if (spec->h == 0.0) {
+    if (oct) {
+        // checked above
+    } else if (spec->h == 0.0) {
         if (!(spec->fill > 1.0) || !isfinite(spec->fill)) {
             set_error("automatic placement needs fill > 1");
             return PB_ERR_ARG;
@@ -236,7 +256,7 @@ pb_status pb_build_grid(const pb_grid_spec *spec, const double *atoms, int64_t n
         return PB_ERR_OOM;
     }
     pb_status st = upload_atoms(g, atoms, atoms_loc, s);
-    if (st == PB_OK) st = grid_build(g, spec, s);
+    if (st == PB_OK) st = oct ? oct_build(g, spec, s) : grid_build(g, spec, s);
     if (st != PB_OK) {
         pb_grid_free(g);
         return st;
@@ -260,6 +280,11 @@ pb_status pb_grid_info_get(const pb_grid *g, pb_grid_info *info) {
     info->n_cross = g->ncross;
     info->n_flux = g->nflux;
     info->n_inside = g->ninside;
+    info->kind = g->is_oct ? PB_GRID_OCTREE : PB_GRID_UNIFORM;
+    info->n_levels = g->is_oct ? g->ot.Lmax + 1 : 1;
+    info->n_bricks = g->is_oct ? g->ot.nb : 0;
+    if (g->is_oct)
+        for (int d = 0; d < 3; ++d) info->n[d] = g->ot.NL + 1;
     return PB_OK;
 }
 
@@ -272,6 +297,7 @@ void pb_system_free(pb_system *s) {
                     s->z32, s->pa32, s->pb32, s->d32, s->z64, s->pa64, s->pb64, s->x64,
                     s->partials, s->queue, s->st, s->Phi, s->Psi, s->ecoul_phi, s->eacc};
     for (void *p : ptrs) dfree(p, st);
+    oct_system_free(s, st);
     cudaStreamSynchronize(st);
     free_tma_state(s);
     if (s->h_st) cudaFreeHost(s->h_st);
@@ -322,9 +348,13 @@ pb_status pb_assemble_coeffs(pb_grid *g, const pb_params *params, void *stream, 
         set_error("pinned host allocation failed");
         st = PB_ERR_OOM;
     }
-    if (st == PB_OK) st = assemble(sys, s);
-    if (st == PB_OK) st = nbody_boundary(sys, s);
-    if (st == PB_OK) st = deposit_rhs(sys, s);
+    if (g->is_oct) {
+        if (st == PB_OK) st = oct_assemble(sys, s);
+    } else {
+        if (st == PB_OK) st = assemble(sys, s);
+        if (st == PB_OK) st = nbody_boundary(sys, s);
+        if (st == PB_OK) st = deposit_rhs(sys, s);
+    }
     if (st != PB_OK) {
         pb_system_free(sys);
         return st;
@@ -343,8 +373,12 @@ pb_status pb_coulomb_terms(pb_system *s, int32_t which, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     pb_status rc = PB_OK;
     if (which & PB_CT_BOUNDARY) {
-        rc = nbody_boundary(s, st);
-        if (rc == PB_OK) rc = deposit_rhs(s, st);
+        if (s->g->is_oct) {
+            rc = oct_boundary_rhs(s, st);
+        } else {
+            rc = nbody_boundary(s, st);
+            if (rc == PB_OK) rc = deposit_rhs(s, st);
+        }
         if (rc == PB_OK) s->solved = 0;
     }
     if (rc == PB_OK && (which & PB_CT_SURFACE)) {
@@ -386,7 +420,7 @@ pb_status pb_solve(pb_system *s, const pb_solve_opts *opts, double *phi_dev, voi
     if (rc != PB_OK) return rc;
     DeviceGuard dg(s->g->device);
     cudaStream_t st = (cudaStream_t)stream;
-    rc = solve(s, opts, st, stats);
+    rc = s->g->is_oct ? oct_solve(s, opts, st, stats) : solve(s, opts, st, stats);
     if (rc == PB_ERR_NOCONV) set_error("solver stopped before reaching rtol");
     if (rc == PB_ERR_TIMEOUT) set_error("solver exceeded its time budget");
     if ((rc == PB_OK || rc == PB_ERR_NOCONV) && phi_dev) {
@@ -407,6 +441,7 @@ pb_status pb_energy(pb_system *s, void *stream, pb_energy_terms *out) {
         return PB_ERR_STATE;
     }
     DeviceGuard dg(s->g->device);
+    if (s->g->is_oct) return oct_energy(s, (cudaStream_t)stream, out);
     return energy(s, (cudaStream_t)stream, out);
 }
 
@@ -442,9 +477,18 @@ pb_status pb_get_array(const pb_grid *g, const pb_system *s, int32_t which, void
         case PB_ARR_CROSS_ALPHA: src = g->calpha; need = 8 * nc; break;
         case PB_ARR_CROSS_RP: src = g->crp; need = 24 * nc; break;
         case PB_ARR_CROSS_SIGN: src = g->csign; need = nc; break;
+        case PB_ARR_OCT_BRICKS:
+        case PB_ARR_OCT_KIND:
+            if (!g->is_oct) {
+                set_error("array %d exists on octree grids only", which);
+                return PB_ERR_ARG;
+            }
+            src = which == PB_ARR_OCT_BRICKS ? (const void *)g->ot.blow : (const void *)g->ot.okind;
+            need = which == PB_ARR_OCT_BRICKS ? 16 * g->ot.nb : g->ot.N;
+            break;
         default: break;
     }
-    if (which >= PB_ARR_WX) {
+    if (which >= PB_ARR_WX && which <= PB_ARR_PSI_SURF) {
         if (!s) {
             set_error("array %d needs a system", which);
             return PB_ERR_ARG;
@@ -477,7 +521,7 @@ pb_status pb_get_array(const pb_grid *g, const pb_system *s, int32_t which, void
                 need = 8 * N;
                 double *t = (double *)dalloc(need, st);
                 if (!t) return PB_ERR_OOM;
-                pb_status rc = fill_kappa(s, t, st);
+                pb_status rc = g->is_oct ? oct_fill_kappa(s, t, st) : fill_kappa(s, t, st);
                 if (rc != PB_OK) return rc;
                 src = t;
                 tmp = true;
@@ -514,6 +558,7 @@ pb_status pb_apply(pb_system *s, int32_t precision, const void *x, void *y, void
         return PB_ERR_ARG;
     }
     DeviceGuard dg(s->g->device);
+    if (s->g->is_oct) return oct_apply(s, precision, x, y, (cudaStream_t)stream);
     return apply_op(s, precision, x, y, (cudaStream_t)stream);
 }
 
@@ -530,6 +575,10 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
         if (!systems[i]) {
             set_error("pb_solve_batch: system %d is NULL", i);
             return PB_ERR_ARG;
+        }
+        if (systems[i]->g->is_oct) {
+            set_error("pb_solve_batch: octree systems are solved by pb_solve");
+            return PB_ERR_UNIMPL;
         }
         if (systems[i]->g->device != systems[0]->g->device) {
             set_error("pb_solve_batch: systems live on different devices");
@@ -587,6 +636,10 @@ pb_status pb_engine_submit(pb_engine *e, pb_system *s, void *stream, int64_t *ti
         set_error("pb_engine_submit: NULL argument");
         return PB_ERR_ARG;
     }
+    if (s->g->is_oct) {
+        set_error("pb_engine_submit: octree systems are solved by pb_solve");
+        return PB_ERR_UNIMPL;
+    }
     DeviceGuard dg(s->g->device);
     long long t = 0;
     pb_status rc = engine_submit(e, s, (cudaStream_t)stream, &t);
@@ -641,6 +694,7 @@ pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int
         return PB_ERR_STATE;
     }
     DeviceGuard dg(s->g->device);
+    if (s->g->is_oct) return oct_profile(s, precision, which, reps, (cudaStream_t)stream);
     return profile_kernels(s, precision, which, reps, (cudaStream_t)stream);
 }
 
@@ -651,6 +705,10 @@ pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_
     if (!s || (precision != PB_FP64 && precision != PB_MIXED)) {
         set_error("pb_set_tuning: bad argument");
         return PB_ERR_ARG;
+    }
+    if (s->g->is_oct) {
+        set_error("pb_set_tuning: octree kernels have no tuning parameters");
+        return PB_ERR_UNIMPL;
     }
     return set_tuning(s, precision, variant, z_chunk);
 }

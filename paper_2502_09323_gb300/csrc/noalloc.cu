@@ -134,6 +134,10 @@ extern "C" pb_status pb_apply_dot_noalloc(const pb_system *s, const double *x, d
         set_error("pb_apply_dot_noalloc: NULL argument");
         return PB_ERR_ARG;
     }
+    if (s->g->is_oct) {
+        set_error("pb_apply_dot_noalloc: octree systems are not supported");
+        return PB_ERR_UNIMPL;
+    }
     const GridGeo &g = s->g->geo;
     const long long blocks = (g.N + NOALLOC_NODES_PER_BLOCK - 1) / NOALLOC_NODES_PER_BLOCK;
     if (blocks > NOALLOC_MAX_BLOCKS) {

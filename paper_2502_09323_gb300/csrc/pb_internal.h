@@ -79,6 +79,38 @@ struct PadGeo {
     long long N;          // canonical nx*ny*nz
 };
 
+// Octree brick grid (device arrays and scalars, passed by value to kernels).
+// Positions are integers in units of the finest spacing ("node units");
+// brick b owns the 8^3 low-corner nodes of its cells, slot 512 b + (8k+j)8+i.
+struct OctDev {
+    double o[3];
+    double hf;            // finest spacing
+    int Lmax, n0, nf, NL; // levels - 1, coarse bricks per axis, finest bricks per axis, side
+    long long nb, N;      // bricks, node slots (512 nb)
+    uint8_t *lev;         // [nf^3] leaf level of each finest-brick cell, (cz*nf+cy)*nf+cx
+    int *bmap;            // [nf^3] leaf brick covering each finest-brick cell
+    int4 *blow;           // [nb] low corner (node units) and level
+    int *bnbr;            // [6 nb] same-level face neighbour (-x,+x,-y,+y,-z,+z); -1 other
+                          // level, -2 outside the domain
+    uint8_t *okind;       // [N] 0 pure row, 1 boundary, 2 hanging, 3 level-transition row
+};
+
+// Level-transition rows of an octree system: explicit CSR of P^T K P.
+struct OctSys {
+    long long ntr, nnz;
+    int *tr_slot;         // [ntr] slot of each row (increasing)
+    int *tr_row;          // [N] row of each slot, -1 if none
+    long long *tr_ptr;    // [ntr + 1]
+    int *tr_col;          // [nnz] column slots, increasing within a row
+    double *tr_val;       // [nnz]
+    float *tr_val32;      // [nnz]
+    double *tr_diag;      // [ntr]
+    double *tpart;        // [4] totals of the transition kernels (sigma, rho, rr)
+    double *partials;     // per-block partials of the transition kernels
+    unsigned int *tcount; // last-block counter of the transition kernels
+    int npart;
+};
+
 }  // namespace pbg
 
 struct pb_grid {
@@ -98,6 +130,10 @@ struct pb_grid {
     int *rowstart;        // [3*ny*nz + 1] first list entry of each edge row
     pbg::BuildInfo *d_info;
     double center[3];     // shift used by the FP32 N-body kernels
+    int is_oct;           // octree grid: geo is the flat slot layout (nx = N)
+    pbg::OctDev ot;
+    pbg::GridGeo vgeo;    // octree: the uniform lattice at the finest spacing
+    long long *cslot_b;   // octree: slot of the +d end of each listed edge
 };
 
 namespace pbg {
@@ -161,6 +197,7 @@ struct pb_system {
     double fnorm2;
     void *tma;          // tensor maps of the FP32 stencil kernels (host object)
     unsigned int *queue;  // work counters of the TMA stencil kernels (device)
+    pbg::OctSys *os;    // octree systems: level-transition rows
 };
 
 namespace pbg {
@@ -192,6 +229,18 @@ pb_status engine_submit(pb_engine *e, pb_system *sys, cudaStream_t s, long long 
 pb_status engine_wait(pb_engine *e, double timeout_s, pb_engine_result *out, int max_out, int *n_out);
 pb_status engine_query(pb_engine *e, int *n_pending, int *n_active, long long *replays);
 pb_status engine_destroy(pb_engine *e);
+
+// ------------------------------------------------------------- octree.cu --
+pb_status oct_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s);
+void oct_grid_free(pb_grid *g, cudaStream_t s);
+pb_status oct_assemble(pb_system *sys, cudaStream_t s);
+pb_status oct_boundary_rhs(pb_system *sys, cudaStream_t s);
+void oct_system_free(pb_system *sys, cudaStream_t s);
+pb_status oct_solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve_stats *st);
+pb_status oct_apply(pb_system *sys, int precision, const void *x, void *y, cudaStream_t s);
+pb_status oct_energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);
+pb_status oct_fill_kappa(const pb_system *sys, double *dst, cudaStream_t s);
+pb_status oct_profile(pb_system *sys, int precision, int which, int reps, cudaStream_t s);
 
 // ------------------------------------------------------------- energy.cu --
 pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);
