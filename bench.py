@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-octree", action="store_true")
+    ap.add_argument("--octree-only", action="store_true",
+                    help="run only the octree workload (for profiling)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=6.0)
@@ -294,6 +297,91 @@ def run_batched(args, pb, pb_inputs, torch):
     return out
 
 
+# ------------------------------------------------------------- octree --
+OCTREE = dict(n_atoms=20000, seed=3, radius=45.0, h_fine=0.25, h_bulk=1.0, refine_dist=3.0,
+              fill=1.5, rtol=1e-8)
+
+
+def run_octree(args, pb, pb_inputs, torch, steps=3, warmup=1, fp64=True):
+    """20,000-atom molecule (45 A ball, seed 3) on a 2:1-balanced brick
+    octree: 0.25 A cells within 3 A of the atom spheres, 1 A bulk; whole hot
+    path per step (build, coefficients, Coulomb terms, mixed solve to 1e-8,
+    energy), and the plain FP64 solve of the same system."""
+    import numpy as np
+    wl = OCTREE
+    atoms = pb_inputs.globular_molecule(wl["n_atoms"], seed=wl["seed"], radius=wl["radius"])
+    atoms_dev = torch.tensor(atoms, device="cuda")
+    spec = pb.OctreeSpec(h_fine=wl["h_fine"], h_bulk=wl["h_bulk"], refine_dist=wl["refine_dist"],
+                         fill=wl["fill"])
+    params = pb.Params()
+
+    def step(precision):
+        g = pb.pb_build_grid(spec, atoms_dev)
+        s = pb.pb_assemble_coeffs(g, params)
+        pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+        st = pb.pb_solve(s, pb.SolveOpts(precision=precision, rtol=wl["rtol"]))
+        return st, pb.pb_energy(s), s
+
+    for _ in range(warmup):
+        step(pb.MIXED)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        st, e, s = step(pb.MIXED)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_step = a.elapsed_time(b) / 1e3 / steps
+    info = s.grid.info
+    kinds = np.bincount(pb.pb_get_array(s.grid, "oct_kind"), minlength=4)
+    out = {
+        "workload": f"{wl['n_atoms']} atoms in a {wl['radius']:g} A ball (seed {wl['seed']}), brick octree "
+                    f"h {wl['h_fine']:g}..{wl['h_bulk']:g} A, refined within {wl['refine_dist']:g} A of "
+                    f"the atom spheres, fill {wl['fill']:g}, eps 2/80, 0.145 M, zero BC, rtol {wl['rtol']:g}",
+        "bricks": int(info.n_bricks), "levels": int(info.n_levels), "slots": int(info.n_nodes),
+        "dof": int(st["dof"]), "transition_rows": int(kinds[3]), "hanging": int(kinds[2]),
+        "crossing_edges": int(info.n_cross),
+        "solves_per_s": 1.0 / t_step, "ms_per_step": 1e3 * t_step,
+        "solve_seconds": st["seconds"], "iters_inner": st["iters_inner"],
+        "iters_outer": st["iters_outer"], "true_rel_res": st["true_rel_res"],
+        "dof_iter_per_s": st["iters_inner"] * st["dof"] / st["seconds"],
+        "energy_kT": e,
+    }
+    # live kernel timing of the brick kernels (pure rows)
+    kt = {}
+    for which, name in ((1, "update"), (0, "direction")):
+        pb.pb_profile_kernels(s, pb.MIXED, which, 3)
+        torch.cuda.synchronize()
+        a.record(stream)
+        pb.pb_profile_kernels(s, pb.MIXED, which, 20)
+        b.record(stream)
+        torch.cuda.synchronize()
+        kt[name] = a.elapsed_time(b) / 1e3 / 20
+    out["kernels"] = {
+        "update_s": kt["update"], "direction_s": kt["direction"],
+        "update_achieved_gbs": info.n_nodes * ALG_BYTES_U32 / kt["update"] / 1e9,
+        "direction_achieved_gbs": info.n_nodes * ALG_BYTES_P32 / kt["direction"] / 1e9,
+        "alg_bytes": "21 B (update) / 13 B (direction) per node slot"}
+    if fp64:
+        del s
+        torch.cuda.synchronize()
+        a.record(stream)
+        st64, e64, s64 = step(pb.FP64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        out["fp64_plain"] = {"solves_per_s": 1.0 / t64, "solve_seconds": st64["seconds"],
+                             "iters": st64["iters_inner"], "true_rel_res": st64["true_rel_res"],
+                             "e_total": e64["e_total"]}
+        out["speedup_mixed_over_fp64"] = t64 / t_step
+        out["energy_rel_diff_mixed_vs_fp64"] = abs(e["e_total"] - e64["e_total"]) / abs(e64["e_total"])
+        del s64
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------ serving --
 def run_serving(args, pb, pb_inputs, torch):
     """Poisson stream of solves (atom counts log-uniform in [300, 50000],
@@ -510,6 +598,7 @@ def run_ours(args, wl):
         smp = oracle_sample(wl, fp64["iters"] if fp64 else None)
         cpu = cpu_baseline_obj(smp)
 
+    octree = None if args.no_octree else run_octree(args, pb, pb_inputs, torch)
     batched = None if args.no_batched else run_batched(args, pb, pb_inputs, torch)
     serving_line = None if args.no_serving else run_serving(args, pb, pb_inputs, torch)
 
@@ -533,6 +622,7 @@ def run_ours(args, wl):
                        "p99": lat_ms[min(len(lat_ms) - 1, math.ceil(0.99 * len(lat_ms)) - 1)]},
         "fp64_plain": fp64,
         "energy_kT": energy,
+        "octree": octree,
         "batched": batched,
         "serving": serving_line,
     }
@@ -548,6 +638,17 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.octree_only:
+        import torch
+
+        import paper_2502_09323_gb300 as pb
+        import pb_inputs
+        from paper_2502_09323_gb300 import build
+        build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"octree": run_octree(args, pb, pb_inputs, torch, steps=args.steps,
+                                               warmup=args.warmup, fp64=not args.no_fp64)}))
+        return 0
     return run_ours(args, wl)
 
 

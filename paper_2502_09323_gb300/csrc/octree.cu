@@ -530,6 +530,12 @@ __global__ void k_oct_coef_special(const long long *__restrict__ ids, const doub
     atomicOr(word, (2u << d) << sh);
 }
 
+// node kind into bits 4-5 of the code byte (read by the brick kernels)
+__global__ void k_oct_code_kind(OctDev t, uint8_t *__restrict__ code) {
+    const long long a = blockIdx.x * (long long)OT + threadIdx.x;
+    if (a < t.N) code[a] = (uint8_t)((code[a] & 15) | (t.okind[a] << 4));
+}
+
 // neighbour slot of slot a (local loc) across direction f (-x,+x,-y,+y,-z,+z);
 // -1 outside the domain or at a different level
 __device__ __forceinline__ long long nbr_slot(const OctDev &t, long long a, int f) {
@@ -1029,76 +1035,183 @@ __device__ __forceinline__ void finalize_u(CgState *s, double t0, double t1) {
     }
 }
 
-// weight of the +d edge starting at slot n (pure-row operator)
-template <typename T>
-__device__ __forceinline__ T edge_w(const OctArgs<T> &A, long long n, int d, int level) {
-    if constexpr (sizeof(T) == 4) {
-        const uint8_t c = A.code[n];
-        if ((c >> (d + 1)) & 1) return A.w32[d][n];
-        return (c & 1) ? A.lc.w_in[level] : A.lc.w_out[level];
-    } else {
-        return A.W[d][n];
-    }
+// Brick kernel of the pure rows: each block stages a brick and its six face
+// halos (the input vector, or p = z + beta p_old for MODE_P, and the code
+// bytes) in shared memory, then applies the 7-point rows of the brick's
+// pure nodes; other nodes are left to the transition kernel.  Bits 4-5 of
+// the code byte hold the node kind.  Dot products: FP32 within a brick,
+// compensated FP32 across a thread's bricks, FP64 across threads and blocks
+// (GB300's FP64 rate is far below its FP32 rate).
+constexpr int SB = 10;  // staged brick side (8 + 2 halo planes)
+
+__device__ __forceinline__ int sidx(int i, int j, int k) { return (i + 1) + SB * ((j + 1) + SB * (k + 1)); }
+
+__device__ __forceinline__ void kahan(float &s, float &c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(OB) k_oct_pure(OctArgs<T> A) {
+__global__ void __launch_bounds__(OB, 6) k_oct_pure(OctArgs<T> A) {
     if (MODE != OM_A && *(volatile int *)&A.st->done) return;
+    __shared__ T sv[SB * SB * SB];
+    __shared__ uint8_t sc[SB * SB * SB];
+    __shared__ int snb[6];
+    __shared__ T slc[3];  // w_in, w_out, kappa of the brick's level
     const OctDev &t = A.t;
     T beta = 0, alpha = 0;
     if (MODE == OM_P) beta = (T)A.st->beta;
     if (MODE == OM_U) alpha = (T)A.st->alpha;
-    double acc0 = 0.0, acc1 = 0.0;
-    for (long long b = blockIdx.x; b < t.nb; b += gridDim.x) {
-        const int level = t.blow[b].w;
+    auto value = [&](int n, uint8_t c) -> T {
+        if (MODE == OM_P) return A.z[n] + beta * A.pold[n];
+        if (MODE == OM_U) return A.p[n];
+        return (c >> 4) == 1 || (c >> 4) == 2 ? (T)0 : A.xin[n];  // boundary entries read as zero
+    };
+    // per-thread sums: FP32 with compensation (FP32 operator) or FP64
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    double d0 = 0.0, d1 = 0.0;
+    const int nb = (int)t.nb;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        __syncthreads();  // the previous brick is done with the staging buffers
+        if (threadIdx.x < 6) snb[threadIdx.x] = t.bnbr[6 * b + threadIdx.x];
+        if (threadIdx.x == 6) {
+            const int level = t.blow[b].w;
+            if constexpr (sizeof(T) == 4) {
+                slc[0] = A.lc.w_in[level];
+                slc[1] = A.lc.w_out[level];
+                slc[2] = A.lc.kap32[level];
+            }
+        }
+        const int base = b << 9;
+        uint8_t cown[2];
+        T vown[2], xown[2], zown[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const long long a = (b << 9) + threadIdx.x + h * OB;
-            const uint8_t kd = t.okind[a];
-            if (kd != 0) {
-                if (MODE == OM_P && kd == 3) A.p[a] = A.z[a] + beta * A.pold[a];
-                if (MODE == OM_A && kd != 3) A.y[a] = (T)0;
+            const int loc = threadIdx.x + h * OB;
+            const int a = base + loc;
+            const uint8_t c = A.code[a];
+            const T v = value(a, c);
+            if (MODE == OM_U) {
+                // issued before the barriers so that their latency overlaps
+                xown[h] = A.x[a];
+                zown[h] = A.zz[a];
+            }
+            const int q = sidx(loc & 7, (loc >> 3) & 7, loc >> 6);
+            sv[q] = v;
+            sc[q] = c;
+            cown[h] = c;
+            vown[h] = v;
+        }
+        __syncthreads();  // snb, slc visible
+        // face halos: 6 faces x 64 nodes; face f = 2d + (side), (u, v) the
+        // two other coordinates in increasing axis order
+        for (int q = threadIdx.x; q < 384; q += OB) {
+            const int f = q >> 6, u = q & 7, v = (q >> 3) & 7;
+            const int d = f >> 1, hi = f & 1;
+            const int nbk = snb[f];
+            const int own = hi ? 8 : -1, other = hi ? 0 : 7;
+            int i, j, k, n;
+            if (d == 0) {
+                i = own; j = u; k = v;
+                n = (k * 8 + j) * 8 + other;
+            } else if (d == 1) {
+                i = u; j = own; k = v;
+                n = (k * 8 + other) * 8 + i;
+            } else {
+                i = u; j = v; k = own;
+                n = (other * 8 + j) * 8 + i;
+            }
+            T val = 0;
+            uint8_t c = 0;
+            if (nbk >= 0) {
+                n += nbk << 9;
+                c = A.code[n];
+                val = value(n, c);
+            }
+            const int sq = sidx(i, j, k);
+            sv[sq] = val;
+            sc[sq] = c;
+        }
+        __syncthreads();
+        float bs0 = 0.f, bs1 = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int loc = threadIdx.x + h * OB;
+            const int a = base + loc;
+            const uint8_t c = cown[h];
+            const int kind = c >> 4;
+            if (kind != 0) {
+                if (MODE == OM_P && kind == 3) A.p[a] = vown[h];
+                if (MODE == OM_A && kind != 3) A.y[a] = (T)0;
                 continue;
             }
-            auto val = [&](long long n) -> T {
-                if (n < 0) return (T)0;
-                if (MODE == OM_P) return A.z[n] + beta * A.pold[n];
-                if (MODE == OM_U) return A.p[n];
-                return t.okind[n] == 1 ? (T)0 : A.xin[n];  // boundary entries read as zero
-            };
-            const T pa = val(a);
+            const int pos[3] = {loc & 7, (loc >> 3) & 7, loc >> 6};
+            const int q = sidx(pos[0], pos[1], pos[2]);
+            const int st3[3] = {1, SB, SB * SB};
+            const int lst[3] = {1, 8, 64};
             T sum = 0, D = 0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const long long m = nbr_slot(t, a, 2 * d), pn = nbr_slot(t, a, 2 * d + 1);
-                const T wm = edge_w<T>(A, m, d, level), wp = edge_w<T>(A, a, d, level);
-                sum += wm * val(m) + wp * val(pn);
+                T wm, wp;
+                if constexpr (sizeof(T) == 4) {
+                    const uint8_t cm = sc[q - st3[d]];
+                    if ((cm >> (d + 1)) & 1) {
+                        // listed edge: its weight lives at the -d neighbour
+                        const int m = pos[d] > 0 ? a - lst[d] : (snb[2 * d] << 9) + loc + 7 * lst[d];
+                        wm = A.w32[d][m];
+                    } else {
+                        wm = (cm & 1) ? slc[0] : slc[1];
+                    }
+                    wp = ((c >> (d + 1)) & 1) ? A.w32[d][a] : ((c & 1) ? slc[0] : slc[1]);
+                } else {
+                    const int m = pos[d] > 0 ? a - lst[d] : (snb[2 * d] << 9) + loc + 7 * lst[d];
+                    wm = A.W[d][m];
+                    wp = A.W[d][a];
+                }
+                sum += wm * sv[q - st3[d]] + wp * sv[q + st3[d]];
                 D = D + wm;
                 D = D + wp;
             }
             if constexpr (sizeof(T) == 4) {
-                D = D + ((A.code[a] & 1) ? 0.f : A.lc.kap32[level]);
+                D = D + ((c & 1) ? 0.f : slc[2]);
             } else {
                 D = A.diag[a];
             }
-            const T q = D * pa - sum;
+            const T pa = vown[h];
+            const T qv = D * pa - sum;
             if (MODE == OM_P) {
                 A.p[a] = pa;
-                acc0 += (double)pa * (double)q;
+                if constexpr (sizeof(T) == 4) bs0 += pa * qv;
+                else d0 += pa * qv;
             } else if (MODE == OM_U) {
-                A.x[a] += alpha * pa;
-                const T zn = A.zz[a] - alpha * q / D;
+                A.x[a] = xown[h] + alpha * pa;
+                const T zn = zown[h] - alpha * qv / D;
                 A.zz[a] = zn;
-                const double dz = (double)D * (double)zn;
-                acc0 += dz * (double)zn;
-                acc1 += dz * dz;
+                const T dz = D * zn;
+                if constexpr (sizeof(T) == 4) {
+                    bs0 += dz * zn;
+                    bs1 += dz * dz;
+                } else {
+                    d0 += dz * zn;
+                    d1 += dz * dz;
+                }
             } else {
-                A.y[a] = q;
+                A.y[a] = qv;
             }
+        }
+        if constexpr (sizeof(T) == 4) {
+            kahan(s0, c0, bs0);
+            kahan(s1, c1, bs1);
         }
     }
     if (MODE == OM_A) return;
-    double mine[2] = {acc0, acc1}, tot[2];
+    if constexpr (sizeof(T) == 4) {
+        d0 = (double)s0 - (double)c0;
+        d1 = (double)s1 - (double)c1;
+    }
+    double mine[2] = {d0, d1}, tot[2];
     if (olast_total<OB, 2>(&A.st->counter, A.partials, mine, tot)) {
         if (threadIdx.x == 0) {
             CgState *s = A.st;
@@ -1661,6 +1774,8 @@ pb_status oct_assemble(pb_system *sys, cudaStream_t s) {
     }
     k_oct_diag<<<cdiv(N, OT), OT, 0, s>>>(t, sys->W[0], sys->W[1], sys->W[2], g->inside, lc,
                                           sys->diag);
+    PB_LAUNCH_CHECK();
+    k_oct_code_kind<<<cdiv(N, OT), OT, 0, s>>>(t, sys->code);
     PB_LAUNCH_CHECK();
     // level-transition rows
     OctSys *os = new (std::nothrow) OctSys();
