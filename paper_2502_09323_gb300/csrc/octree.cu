@@ -1035,16 +1035,17 @@ __device__ __forceinline__ void finalize_u(CgState *s, double t0, double t1) {
     }
 }
 
-// Brick kernel of the pure rows: each block stages a brick and its six face
-// halos (the input vector, or p = z + beta p_old for MODE_P, and the code
-// bytes) in shared memory, then applies the 7-point rows of the brick's
-// pure nodes; other nodes are left to the transition kernel.  Bits 4-5 of
-// the code byte hold the node kind.  Dot products: FP32 within a brick,
-// compensated FP32 across a thread's bricks, FP64 across threads and blocks
-// (GB300's FP64 rate is far below its FP32 rate).
-constexpr int SB = 10;  // staged brick side (8 + 2 halo planes)
-
-__device__ __forceinline__ int sidx(int i, int j, int k) { return (i + 1) + SB * ((j + 1) + SB * (k + 1)); }
+// Brick kernel of the pure rows.  A block works on four bricks at a time,
+// 64 threads per brick, each thread owning the z-column (i, j) of its brick:
+// the column's values stay in registers (its z neighbours), the brick's
+// planes with their x/y face halos are staged in shared memory, and each
+// brick's 64 threads synchronise on their own named barrier.  Only pure
+// nodes are applied here; level-transition rows go to the CSR kernel.  Bits
+// 4-5 of the code byte hold the node kind.  Dot products: FP32 within a
+// brick, compensated FP32 across a thread's bricks, FP64 across threads and
+// blocks (GB300's FP64 rate is far below its FP32 rate).
+constexpr int PX = 10;         // staged plane side (8 + 2 halo lines)
+constexpr int PP = PX * PX;    // staged plane size
 
 __device__ __forceinline__ void kahan(float &s, float &c, float v) {
     const float y = v - c;
@@ -1053,141 +1054,157 @@ __device__ __forceinline__ void kahan(float &s, float &c, float v) {
     s = t;
 }
 
+// named barrier of one 64-thread brick group (ids 1-4; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int g) {
+    switch (g) {
+        case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+        case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+        case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+        default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+    }
+}
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(OB, 6) k_oct_pure(OctArgs<T> A) {
+__global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T> A) {
     if (MODE != OM_A && *(volatile int *)&A.st->done) return;
-    __shared__ T sv[SB * SB * SB];
-    __shared__ uint8_t sc[SB * SB * SB];
-    __shared__ int snb[6];
-    __shared__ T slc[3];  // w_in, w_out, kappa of the brick's level
+    __shared__ T sv[4][8 * PP];
+    __shared__ uint8_t sc[4][8 * PP];
+    __shared__ int snb[4][6];
     const OctDev &t = A.t;
+    const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
+    const int i = c & 7, j = c >> 3;
     T beta = 0, alpha = 0;
     if (MODE == OM_P) beta = (T)A.st->beta;
     if (MODE == OM_U) alpha = (T)A.st->alpha;
-    auto value = [&](int n, uint8_t c) -> T {
+    auto value = [&](int n, uint8_t cd) -> T {
         if (MODE == OM_P) return A.z[n] + beta * A.pold[n];
         if (MODE == OM_U) return A.p[n];
-        return (c >> 4) == 1 || (c >> 4) == 2 ? (T)0 : A.xin[n];  // boundary entries read as zero
+        return (cd >> 4) == 1 || (cd >> 4) == 2 ? (T)0 : A.xin[n];  // boundary entries read as zero
     };
-    // per-thread sums: FP32 with compensation (FP32 operator) or FP64
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
     double d0 = 0.0, d1 = 0.0;
     const int nb = (int)t.nb;
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        __syncthreads();  // the previous brick is done with the staging buffers
-        if (threadIdx.x < 6) snb[threadIdx.x] = t.bnbr[6 * b + threadIdx.x];
-        if (threadIdx.x == 6) {
-            const int level = t.blow[b].w;
-            if constexpr (sizeof(T) == 4) {
-                slc[0] = A.lc.w_in[level];
-                slc[1] = A.lc.w_out[level];
-                slc[2] = A.lc.kap32[level];
-            }
+    T *V = sv[g];
+    uint8_t *C = sc[g];
+    const int q0 = (j + 1) * PX + (i + 1);  // this column's position in a staged plane
+    for (int b = blockIdx.x * 4 + g; b < nb; b += gridDim.x * 4) {
+        group_sync(g);  // the group's previous brick is done with its buffers
+        if (c < 6) snb[g][c] = t.bnbr[6 * b + c];
+        const int level = t.blow[b].w;
+        T wi = 0, wo = 0, kp = 0;
+        if constexpr (sizeof(T) == 4) {
+            wi = A.lc.w_in[level];
+            wo = A.lc.w_out[level];
+            kp = A.lc.kap32[level];
         }
-        const int base = b << 9;
-        uint8_t cown[2];
-        T vown[2], xown[2], zown[2];
+        const int base = (b << 9) + c;
+        T v[8], xr[MODE == OM_U ? 8 : 1], zr[MODE == OM_U ? 8 : 1];
+        uint8_t cd[8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int loc = threadIdx.x + h * OB;
-            const int a = base + loc;
-            const uint8_t c = A.code[a];
-            const T v = value(a, c);
-            if (MODE == OM_U) {
+        for (int k = 0; k < 8; ++k) {
+            cd[k] = A.code[base + 64 * k];
+            v[k] = value(base + 64 * k, cd[k]);
+            if constexpr (MODE == OM_U) {
                 // issued before the barriers so that their latency overlaps
-                xown[h] = A.x[a];
-                zown[h] = A.zz[a];
+                xr[k] = A.x[base + 64 * k];
+                zr[k] = A.zz[base + 64 * k];
             }
-            const int q = sidx(loc & 7, (loc >> 3) & 7, loc >> 6);
-            sv[q] = v;
-            sc[q] = c;
-            cown[h] = c;
-            vown[h] = v;
+            V[k * PP + q0] = v[k];
+            C[k * PP + q0] = cd[k];
         }
-        __syncthreads();  // snb, slc visible
-        // face halos: 6 faces x 64 nodes; face f = 2d + (side), (u, v) the
-        // two other coordinates in increasing axis order
-        for (int q = threadIdx.x; q < 384; q += OB) {
-            const int f = q >> 6, u = q & 7, v = (q >> 3) & 7;
-            const int d = f >> 1, hi = f & 1;
-            const int nbk = snb[f];
-            const int own = hi ? 8 : -1, other = hi ? 0 : 7;
-            int i, j, k, n;
-            if (d == 0) {
-                i = own; j = u; k = v;
-                n = (k * 8 + j) * 8 + other;
-            } else if (d == 1) {
-                i = u; j = own; k = v;
-                n = (k * 8 + other) * 8 + i;
-            } else {
-                i = u; j = v; k = own;
-                n = (other * 8 + j) * 8 + i;
+        group_sync(g);  // snb visible
+        // x/y face halos: 4 faces x 64 values, 4 per thread
+        {
+            const int f = c >> 4;  // 0 -x, 1 +x, 2 -y, 3 +y
+            const int nbk = snb[g][f];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = (c & 15) + 16 * r;
+                const int u = m & 7, k = m >> 3;
+                int sq, n;
+                if (f < 2) {
+                    sq = k * PP + (u + 1) * PX + (f == 0 ? 0 : 9);
+                    n = (k * 8 + u) * 8 + (f == 0 ? 7 : 0);
+                } else {
+                    sq = k * PP + (f == 2 ? 0 : 9) * PX + (u + 1);
+                    n = (k * 8 + (f == 2 ? 7 : 0)) * 8 + u;
+                }
+                T val = 0;
+                uint8_t cc = 0;
+                if (nbk >= 0) {
+                    n += nbk << 9;
+                    cc = A.code[n];
+                    val = value(n, cc);
+                }
+                V[sq] = val;
+                C[sq] = cc;
             }
-            T val = 0;
-            uint8_t c = 0;
-            if (nbk >= 0) {
-                n += nbk << 9;
-                c = A.code[n];
-                val = value(n, c);
-            }
-            const int sq = sidx(i, j, k);
-            sv[sq] = val;
-            sc[sq] = c;
         }
-        __syncthreads();
+        // z halos of this column and the -z neighbour's code
+        const int nzm = snb[g][4], nzp = snb[g][5];
+        T zm = 0, zp = 0;
+        uint8_t czm = 0;
+        if (nzm >= 0) {
+            const int n = (nzm << 9) + 448 + c;
+            czm = A.code[n];
+            zm = value(n, czm);
+        }
+        if (nzp >= 0) zp = value((nzp << 9) + c, A.code[(nzp << 9) + c]);
+        group_sync(g);
         float bs0 = 0.f, bs1 = 0.f;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int loc = threadIdx.x + h * OB;
-            const int a = base + loc;
-            const uint8_t c = cown[h];
-            const int kind = c >> 4;
+        for (int k = 0; k < 8; ++k) {
+            const int a = base + 64 * k;
+            const uint8_t cc = cd[k];
+            const int kind = cc >> 4;
             if (kind != 0) {
-                if (MODE == OM_P && kind == 3) A.p[a] = vown[h];
+                if (MODE == OM_P && kind == 3) A.p[a] = v[k];
                 if (MODE == OM_A && kind != 3) A.y[a] = (T)0;
                 continue;
             }
-            const int pos[3] = {loc & 7, (loc >> 3) & 7, loc >> 6};
-            const int q = sidx(pos[0], pos[1], pos[2]);
-            const int st3[3] = {1, SB, SB * SB};
-            const int lst[3] = {1, 8, 64};
-            T sum = 0, D = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                T wm, wp;
-                if constexpr (sizeof(T) == 4) {
-                    const uint8_t cm = sc[q - st3[d]];
-                    if ((cm >> (d + 1)) & 1) {
-                        // listed edge: its weight lives at the -d neighbour
-                        const int m = pos[d] > 0 ? a - lst[d] : (snb[2 * d] << 9) + loc + 7 * lst[d];
-                        wm = A.w32[d][m];
-                    } else {
-                        wm = (cm & 1) ? slc[0] : slc[1];
-                    }
-                    wp = ((c >> (d + 1)) & 1) ? A.w32[d][a] : ((c & 1) ? slc[0] : slc[1]);
-                } else {
-                    const int m = pos[d] > 0 ? a - lst[d] : (snb[2 * d] << 9) + loc + 7 * lst[d];
-                    wm = A.W[d][m];
-                    wp = A.W[d][a];
-                }
-                sum += wm * sv[q - st3[d]] + wp * sv[q + st3[d]];
-                D = D + wm;
-                D = D + wp;
-            }
+            const int q = k * PP + q0;
+            const T xm = V[q - 1], xp = V[q + 1], ym = V[q - PX], yp = V[q + PX];
+            const T zmv = k > 0 ? v[k - 1] : zm, zpv = k < 7 ? v[k + 1] : zp;
+            T w[6];  // -x, +x, -y, +y, -z, +z
             if constexpr (sizeof(T) == 4) {
-                D = D + ((c & 1) ? 0.f : slc[2]);
+                const uint8_t cxm = C[q - 1], cym = C[q - PX];
+                const uint8_t czmk = k > 0 ? cd[k - 1] : czm;
+                const T wself = (cc & 1) ? wi : wo;
+                w[1] = (cc & 2) ? A.w32[0][a] : wself;
+                w[3] = (cc & 4) ? A.w32[1][a] : wself;
+                w[5] = (cc & 8) ? A.w32[2][a] : wself;
+                if (cxm & 2) w[0] = A.w32[0][i > 0 ? a - 1 : (snb[g][0] << 9) + (a & 511) + 7];
+                else w[0] = (cxm & 1) ? wi : wo;
+                if (cym & 4) w[2] = A.w32[1][j > 0 ? a - 8 : (snb[g][2] << 9) + (a & 511) + 56];
+                else w[2] = (cym & 1) ? wi : wo;
+                if (czmk & 8) w[4] = A.w32[2][k > 0 ? a - 64 : (nzm << 9) + (a & 511) + 448];
+                else w[4] = (czmk & 1) ? wi : wo;
+            } else {
+                w[0] = A.W[0][i > 0 ? a - 1 : (snb[g][0] << 9) + (a & 511) + 7];
+                w[1] = A.W[0][a];
+                w[2] = A.W[1][j > 0 ? a - 8 : (snb[g][2] << 9) + (a & 511) + 56];
+                w[3] = A.W[1][a];
+                w[4] = A.W[2][k > 0 ? a - 64 : (nzm << 9) + (a & 511) + 448];
+                w[5] = A.W[2][a];
+            }
+            const T sum = w[0] * xm + w[1] * xp + w[2] * ym + w[3] * yp + w[4] * zmv + w[5] * zpv;
+            T D;
+            if constexpr (sizeof(T) == 4) {
+                D = (((((w[0] + w[1]) + w[2]) + w[3]) + w[4]) + w[5]) + ((cc & 1) ? (T)0 : kp);
             } else {
                 D = A.diag[a];
             }
-            const T pa = vown[h];
+            const T pa = v[k];
             const T qv = D * pa - sum;
             if (MODE == OM_P) {
                 A.p[a] = pa;
                 if constexpr (sizeof(T) == 4) bs0 += pa * qv;
                 else d0 += pa * qv;
             } else if (MODE == OM_U) {
-                A.x[a] = xown[h] + alpha * pa;
-                const T zn = zown[h] - alpha * qv / D;
+                A.x[a] = xr[k] + alpha * pa;
+                T zn;
+                if constexpr (sizeof(T) == 4) zn = zr[k] - __fdividef(alpha * qv, D);
+                else zn = zr[k] - alpha * qv / D;
                 A.zz[a] = zn;
                 const T dz = D * zn;
                 if constexpr (sizeof(T) == 4) {
@@ -1433,15 +1450,17 @@ BcDesc bc_desc(const pb_system *sys) {
     return bd;
 }
 
+// persistent grid of a brick kernel: its resident blocks per SM x SMs
+template <typename T, int MODE>
 int pure_grid() {
     static int g = 0;
     if (!g) {
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oct_pure<float, OM_U>, OB, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oct_pure<T, MODE>, OB, 0) !=
                 cudaSuccess ||
             per <= 0) {
             cudaGetLastError();
-            per = 4;
+            per = 3;
         }
         g = per * num_sms();
     }
@@ -1911,11 +1930,10 @@ void oct_iteration(pb_system *sys, OctArgs<T> A, T *z, T *pold, T *p, T *x, cuda
     A.p = p;
     A.x = x;
     A.zz = z;
-    const int G = pure_grid();
     if (A.ntr > 0) k_oct_trans<T, OM_P><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
-    k_oct_pure<T, OM_P><<<G, OB, 0, s>>>(A);
+    k_oct_pure<T, OM_P><<<pure_grid<T, OM_P>(), OB, 0, s>>>(A);
     if (A.ntr > 0) k_oct_trans<T, OM_U><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
-    k_oct_pure<T, OM_U><<<G, OB, 0, s>>>(A);
+    k_oct_pure<T, OM_U><<<pure_grid<T, OM_U>(), OB, 0, s>>>(A);
     note_launch(A.ntr > 0 ? 4 : 2);
 }
 
@@ -1926,7 +1944,9 @@ pb_status oct_ensure_ws(pb_system *sys, int precision, cudaStream_t s) {
         if (!sys->st) return PB_ERR_OOM;
         PB_CUDA_TRY(cudaMemsetAsync(sys->st, 0, sizeof(CgState), s));
         PB_CUDA_TRY(cudaMallocHost((void **)&sys->h_st, 4 * sizeof(CgState)));
-        sys->npartials = 2 * (int)std::max<long long>(cdiv(N, OT), pure_grid()) + 64;
+        const int G = std::max(std::max(pure_grid<float, OM_P>(), pure_grid<float, OM_U>()),
+                               std::max(pure_grid<double, OM_P>(), pure_grid<double, OM_U>()));
+        sys->npartials = 2 * (int)std::max<long long>(cdiv(N, OT), G) + 64;
         sys->partials = (double *)dalloc(sizeof(double) * sys->npartials, s);
         if (!sys->partials) return PB_ERR_OOM;
     }
@@ -2176,12 +2196,11 @@ pb_status oct_apply(pb_system *sys, int precision, const void *x, void *y, cudaS
         pb_status rc = oct_ensure_ws(sys, precision, s);
         if (rc != PB_OK) return rc;
     }
-    const int G = pure_grid();
     if (precision == PB_MIXED) {
         OctArgs<float> A = oct_args<float>(sys);
         A.xin = (const float *)x;
         A.y = (float *)y;
-        k_oct_pure<float, OM_A><<<G, OB, 0, s>>>(A);
+        k_oct_pure<float, OM_A><<<pure_grid<float, OM_A>(), OB, 0, s>>>(A);
         PB_LAUNCH_CHECK();
         if (A.ntr > 0) {
             k_oct_trans<float, OM_A><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
@@ -2191,7 +2210,7 @@ pb_status oct_apply(pb_system *sys, int precision, const void *x, void *y, cudaS
         OctArgs<double> A = oct_args<double>(sys);
         A.xin = (const double *)x;
         A.y = (double *)y;
-        k_oct_pure<double, OM_A><<<G, OB, 0, s>>>(A);
+        k_oct_pure<double, OM_A><<<pure_grid<double, OM_A>(), OB, 0, s>>>(A);
         PB_LAUNCH_CHECK();
         if (A.ntr > 0) {
             k_oct_trans<double, OM_A><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
@@ -2205,7 +2224,6 @@ pb_status oct_apply(pb_system *sys, int precision, const void *x, void *y, cudaS
 pb_status oct_profile(pb_system *sys, int precision, int which, int reps, cudaStream_t s) {
     pb_status rc = oct_state(sys, 1.0, 1.0, -1.0, 1 << 30, s, 1);
     if (rc != PB_OK) return rc;
-    const int G = pure_grid();
     for (int r = 0; r < reps; ++r) {
         if (precision == PB_MIXED) {
             OctArgs<float> A = oct_args<float>(sys);
@@ -2213,16 +2231,16 @@ pb_status oct_profile(pb_system *sys, int precision, int which, int reps, cudaSt
             A.pold = (r & 1) ? sys->pb32 : sys->pa32;
             A.p = (r & 1) ? sys->pa32 : sys->pb32;
             A.x = sys->d32;
-            if (which == 0 || which == 2) k_oct_pure<float, OM_P><<<G, OB, 0, s>>>(A);
-            if (which == 1 || which == 2) k_oct_pure<float, OM_U><<<G, OB, 0, s>>>(A);
+            if (which == 0 || which == 2) k_oct_pure<float, OM_P><<<pure_grid<float, OM_P>(), OB, 0, s>>>(A);
+            if (which == 1 || which == 2) k_oct_pure<float, OM_U><<<pure_grid<float, OM_U>(), OB, 0, s>>>(A);
         } else {
             OctArgs<double> A = oct_args<double>(sys);
             A.z = A.zz = sys->z64;
             A.pold = (r & 1) ? sys->pb64 : sys->pa64;
             A.p = (r & 1) ? sys->pa64 : sys->pb64;
             A.x = sys->x64;
-            if (which == 0 || which == 2) k_oct_pure<double, OM_P><<<G, OB, 0, s>>>(A);
-            if (which == 1 || which == 2) k_oct_pure<double, OM_U><<<G, OB, 0, s>>>(A);
+            if (which == 0 || which == 2) k_oct_pure<double, OM_P><<<pure_grid<double, OM_P>(), OB, 0, s>>>(A);
+            if (which == 1 || which == 2) k_oct_pure<double, OM_U><<<pure_grid<double, OM_U>(), OB, 0, s>>>(A);
         }
         PB_LAUNCH_CHECK();
     }
