@@ -444,6 +444,24 @@ def run_serving(args, pb, pb_inputs, torch):
     return out
 
 
+# ------------------------------------------------------------- ranks --
+def max_over_ranks_of(v: float, dist, device) -> float:
+    """Largest value over all ranks (the slowest rank's time); v itself
+    without a process group."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps: int, world: int, elapsed_max_s: float) -> float:
+    """Units processed by all ranks (one workload copy per rank and step)
+    per second of the slowest rank."""
+    return steps * world / elapsed_max_s
+
+
 # ------------------------------------------------------------------ ours --
 def run_ours(args, wl):
     import numpy as np
@@ -490,11 +508,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(v, dist, dev)
 
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -521,7 +535,7 @@ def run_ours(args, wl):
     clk = clocks.stop()
     launches = pb.pb_kernel_launches() - launches0
     elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
-    value = args.steps * world / elapsed
+    value = whole_job_rate(args.steps, world, elapsed)
     energy = e
     dof = stats[-1]["dof"]
     iters = statistics.mean(s_["iters_inner"] for s_ in stats)
@@ -611,7 +625,7 @@ def run_ours(args, wl):
         "config": config_obj(args, wl),
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": args.steps * world / e2e_elapsed, "unit": "solves/s",
+        "e2e": {"value": whole_job_rate(args.steps, world, e2e_elapsed), "unit": "solves/s",
                 "h2d_bytes_per_step": int(atoms_np.nbytes), "d2h_bytes_per_step": 48},
         "gpu_launches": int(launches),
         "clocks": clk,

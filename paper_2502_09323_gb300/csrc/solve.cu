@@ -675,9 +675,13 @@ template <int MODE>
 pb_status tma_prepare() {
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<MODE, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              tma::smem_bytes<MODE>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stencil_tma<MODE, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tma::smem_bytes<MODE>());
         if (e != cudaSuccess) {
             set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
             return PB_ERR_CUDA;
@@ -693,7 +697,7 @@ dim3 tma_grid(const PadGeo &g, int) {
     static int per_sm = 0;
     if (!per_sm) {
         if (tma_prepare<MODE_U>() != PB_OK ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<MODE_U>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<MODE_U, false>,
                                                           tma::NTHREADS,
                                                           tma::smem_bytes<MODE_U>()) != cudaSuccess ||
             per_sm <= 0) {
@@ -706,9 +710,17 @@ dim3 tma_grid(const PadGeo &g, int) {
 
 template <int MODE>
 void tma_launch(const tma::SysEntry *dev_tab, int nsys, int total_items, unsigned int *queue,
-                dim3 grid, cudaStream_t s) {
-    k_stencil_tma<MODE><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(dev_tab, nsys,
-                                                                           total_items, queue);
+                dim3 grid, cudaStream_t s, const tma::SysEntry *host_e0 = nullptr) {
+    // host_e0: the host copy of the entry of a one-system launch, passed by
+    // value (the single-system kernel reads everything of it from the
+    // parameter bank); nullptr or several systems: the table form
+    static const tma::SysEntry zero{};
+    if (host_e0 && nsys == 1)
+        k_stencil_tma<MODE, true><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(
+            dev_tab, nsys, total_items, queue, *host_e0);
+    else
+        k_stencil_tma<MODE, false><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(
+            dev_tab, nsys, total_items, queue, zero);
 }
 
 struct TmaState {
@@ -800,8 +812,8 @@ void launch_iter_tma(pb_system *sys, const CoefC32 &, int cur, int KC, cudaStrea
     TmaState *t = (TmaState *)sys->tma;
     if (tma_use_kc(sys, KC, s) != PB_OK) return;
     dim3 grid = tma_grid(sys->pad, KC);
-    tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
-    tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
+    tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
+    tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
 }
 
 CoefC32 make_c32(const pb_system *sys) {
@@ -1321,11 +1333,11 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
             if ((rc = tma_use_kc(sys, KC, s)) != PB_OK) return rc;
             dim3 grid = tma_grid(sys->pad, KC);
             if (which == 0 || which == 2) {
-                tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
+                tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
                 PB_LAUNCH_CHECK();
             }
             if (which == 1 || which == 2) {
-                tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s);
+                tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
                 PB_LAUNCH_CHECK();
             }
         } else if (precision == PB_MIXED) {
@@ -1420,12 +1432,13 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
         cudaError_t ce = cudaMemcpyAsync(de, e, sizeof(tma::SysEntry), cudaMemcpyHostToDevice, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         const int nitems = e->nitems;
-        delete e;
         if (ce != cudaSuccess) {
+            delete e;
             set_error("apply table upload: %s", cudaGetErrorString(ce));
             return PB_ERR_CUDA;
         }
-        tma_launch<MODE_A>(de, 1, nitems, sys->queue, tma_grid(p, 8), s);
+        tma_launch<MODE_A>(de, 1, nitems, sys->queue, tma_grid(p, 8), s, e);
+        delete e;
         PB_LAUNCH_CHECK();
         dfree(de, s);
         k_pad_to_canon<float><<<blocks, 256, 0, s>>>((const float *)yp, (float *)y, g, p);
@@ -1558,8 +1571,8 @@ pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, 
             break;
         }
         for (int c = 0; c < chunk; ++c) {
-            tma_launch<MODE_P>(dtab, n, total, queue, grid, cs);
-            tma_launch<MODE_U>(dtab, n, total, queue, grid, cs);
+            tma_launch<MODE_P>(dtab, n, total, queue, grid, cs, &tab[0]);
+            tma_launch<MODE_U>(dtab, n, total, queue, grid, cs, &tab[0]);
         }
         if (cudaStreamEndCapture(cs, &graph) != cudaSuccess ||
             cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {

@@ -145,6 +145,12 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -158,15 +164,23 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // nsys < 0 the table size and item total are read from queue[2] and
 // queue[3], so a captured launch follows a table that changes between
 // replays.
-template <int MODE>
+// SINGLE: a launch over one system whose table entry (tensor maps,
+// geometry, coefficients) is the kernel parameter e0, so that its values are
+// read from the parameter bank instead of occupying registers; the
+// arithmetic is the same as in the table form.
+template <int MODE, bool SINGLE>
 __global__ void __launch_bounds__(tma::NTHREADS, 2)
 k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
-              unsigned int *queue) {
+              unsigned int *queue, const __grid_constant__ tma::SysEntry e0) {
     using namespace tma;
     using L = SlotLayout<MODE>;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort, s_nsys, s_total;
     __shared__ int s_desc[NSLOT][7];  // i0, j0, kfirst, len, system, local item, parity
+    // per-descriptor warp partials of the dot products, combined without a
+    // barrier: the warp that completes a descriptor's count sums them
+    __shared__ double s_part[NSLOT][ROWS][2];
+    __shared__ unsigned s_pcnt[NSLOT];
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NSLOT * L::stride);
@@ -178,6 +192,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
+        for (int q = 0; q < NSLOT; ++q) s_pcnt[q] = 0u;
         s_nsys = nsys < 0 ? (int)((volatile unsigned int *)queue)[2] : nsys;
         s_total = nsys < 0 ? (int)((volatile unsigned int *)queue)[3] : total_items;
     }
@@ -191,22 +206,38 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             int last_use[NSLOT];
             for (int s = 0; s < NSLOT; ++s) last_use[s] = -1;
             int gt = 0, nseg = 0;  // running plane and chunk counters
+            // a system's done flag and parity cannot change during this
+            // launch before all its items are consumed (only its finaliser
+            // changes them), so they are read once per system, not per item
+            int csys = -1, cdone = 0, ccur = 0;
             for (;;) {
                 const int item = (int)atomicAdd(queue, 1u);
                 const bool end = item >= total_items;
                 int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1, cur = 0;
                 const SysEntry *e = tab;
                 if (!end) {
-                    int lo = 0, hi = nsys - 1;  // last entry with item_base <= item
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (tab[mid].item_base <= item) lo = mid;
-                        else hi = mid - 1;
+                    if constexpr (SINGLE) {
+                        sys = 0;
+                        e = &e0;
+                    } else {
+                        int lo = 0, hi = nsys - 1;  // last entry with item_base <= item
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (tab[mid].item_base <= item) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        sys = lo;
+                        e = tab + sys;
                     }
-                    sys = lo;
-                    e = tab + sys;
-                    if (MODE != MODE_A && *(volatile int *)&e->st->done) continue;  // converged
-                    if (MODE != MODE_A) cur = *(volatile int *)&e->st->cur;
+                    if (MODE != MODE_A) {
+                        if (sys != csys) {
+                            cdone = *(volatile int *)&e->st->done;
+                            ccur = *(volatile int *)&e->st->cur;
+                            csys = sys;
+                        }
+                        if (cdone) continue;  // converged
+                        cur = ccur;
+                    }
                     li = item - e->item_base;
                     const int col = li / e->nchunk, c = li - col * e->nchunk;
                     kfirst = 1 + c * e->KC;
@@ -306,6 +337,29 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         };
 
         int gt = 0, nseg = 0;
+        // per-system values, reloaded only when the system changes (they
+        // cannot change during the launch: finalisation runs at its end)
+        int ksys = -1;
+        PadGeo g{};
+        CoefC32 cp{};
+        float alpha = 0.f, dg_in = 0.f, dg_out = 0.f, dinv_in = 0.f, dinv_out = 0.f;
+        float *pb0 = nullptr, *pb1 = nullptr, *yg = nullptr, *xg = nullptr, *zg = nullptr;
+        if constexpr (SINGLE) {
+            g = e0.pg;
+            cp = e0.cp;
+            if (MODE == MODE_P) beta = (float)e0.st->beta;
+            if (MODE == MODE_U) alpha = (float)e0.st->alpha;
+            dg_in = 6.f * cp.w_in;
+            dg_out = 6.f * cp.w_out + cp.kap;
+            dinv_in = 1.f / dg_in;
+            dinv_out = 1.f / dg_out;
+            pb0 = e0.pbuf[0];
+            pb1 = e0.pbuf[1];
+            yg = e0.y;
+            xg = e0.x;
+            zg = e0.z;
+            ksys = 0;
+        }
         for (;; ++nseg) {
             // the chunk's first plane's barrier also publishes its descriptor
             if (!wait_full(gt)) break;
@@ -313,16 +367,24 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             const int len = d[3];
             if (len < 0) break;  // end of work
             const int i0 = d[0], j0 = d[1], kfirst = d[2], sys = d[4], li = d[5], cur = d[6];
-            const SysEntry *e = tab + sys;
-            const PadGeo g = e->pg;
-            const CoefC32 cp = e->cp;
-            float alpha = 0.f;
-            if (MODE == MODE_P) beta = (float)e->st->beta;
-            if (MODE == MODE_U) alpha = (float)e->st->alpha;
-            const float dg_in = 6.f * cp.w_in, dg_out = 6.f * cp.w_out + cp.kap;
-            const float dinv_in = 1.f / dg_in, dinv_out = 1.f / dg_out;
-            float *const outp = MODE == MODE_P ? e->pbuf[cur ^ 1] : (MODE == MODE_A ? e->y : nullptr);
-            float *const xg = e->x, *const zg = e->z;
+            const SysEntry *e = SINGLE ? &e0 : tab + sys;
+            if (!SINGLE && sys != ksys) {
+                g = e->pg;
+                cp = e->cp;
+                if (MODE == MODE_P) beta = (float)e->st->beta;
+                if (MODE == MODE_U) alpha = (float)e->st->alpha;
+                dg_in = 6.f * cp.w_in;
+                dg_out = 6.f * cp.w_out + cp.kap;
+                dinv_in = 1.f / dg_in;
+                dinv_out = 1.f / dg_out;
+                pb0 = e->pbuf[0];
+                pb1 = e->pbuf[1];
+                yg = e->y;
+                xg = e->x;
+                zg = e->z;
+                ksys = sys;
+            }
+            float *const outp = MODE == MODE_P ? (cur ? pb0 : pb1) : (MODE == MODE_A ? yg : nullptr);
             const int j = j0 + w;
             const int ib = i0 + lane * 4;
             const bool active = j <= g.ny - 2;
@@ -525,78 +587,41 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             gt = gt0 + len + 2;
             if (MODE == MODE_A) continue;
 
-            // ---- this warp's dot products of this item -> their own slot;
-            // the warp that fills a system's last slot sums all slots in a
-            // fixed order and updates that system's CG state (no barriers)
-            const double b0 = warp_sum_d((double)acc0), b1 = warp_sum_d((double)acc1);
-            const int nslots = e->nitems * ROWS;
-            unsigned last = 0;
+            // ---- dot products of this item: the 8 row warps combine their
+            // partials in shared memory (the warp that completes the count
+            // sums them in row order) and that warp stores the item's partial.
+            // The last block of the launch sums each system's item partials
+            // in item order and updates its CG state.  No warp waits for
+            // another.
+            // (FP32 across the warp: the FP64 pipe of this part is narrow)
+            const float b0 = warp_sum_f(acc0), b1 = warp_sum_f(acc1);
+            const int ps = nseg % NSLOT;
             if (lane == 0) {
-                const int idx = li * ROWS + w;
-                if (MODE == MODE_P) {
-                    e->partials[idx] = b0;
-                } else {
-                    e->partials[nslots + 2 * idx] = b0;
-                    e->partials[nslots + 2 * idx + 1] = b1;
-                }
-                __threadfence();
-                last = atomicAdd(e->cnt, 1u) == (unsigned)nslots - 1;
-            }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
-                __threadfence();
-                double t0 = 0.0, t1 = 0.0;
-                for (int q = lane; q < nslots; q += 32) {
-                    if (MODE == MODE_P) {
-                        t0 += __ldcg(e->partials + q);
-                    } else {
-                        t0 += __ldcg(e->partials + nslots + 2 * q);
-                        t1 += __ldcg(e->partials + nslots + 2 * q + 1);
+                s_part[ps][w][0] = (double)b0;
+                s_part[ps][w][1] = (double)b1;
+                __threadfence_block();
+                if (atomicAdd(&s_pcnt[ps], 1u) == (unsigned)ROWS - 1) {
+                    __threadfence_block();
+                    double t0 = 0.0, t1 = 0.0;
+                    for (int r = 0; r < ROWS; ++r) {
+                        t0 += *(volatile double *)&s_part[ps][r][0];
+                        t1 += *(volatile double *)&s_part[ps][r][1];
                     }
-                }
-                t0 = warp_sum_d(t0);
-                t1 = warp_sum_d(t1);
-                if (lane == 0) {
-                    CgState *st = e->st;
+                    s_pcnt[ps] = 0u;
+                    const int nit = e->nitems;
                     if (MODE == MODE_P) {
-                        st->sigma = t0;
-                        if (st->status == 3) {
-                            st->done = 1;
-                        } else if (st->profile) {
-                            st->alpha = isfinite(t0) && t0 != 0.0 ? st->rho / t0 : 0.0;
-                        } else if (!(t0 > 0.0) || !isfinite(t0)) {
-                            st->done = 1;
-                            st->status = 1;
-                        } else {
-                            st->alpha = st->rho / t0;
-                        }
+                        e->partials[li] = t0;
                     } else {
-                        st->beta = t0 / st->rho;
-                        st->rho = t0;
-                        st->rr = t1;
-                        st->iter += 1;
-                        st->cur ^= 1;  // the new p_old is this iteration's p
-                        if (st->status == 3) {
-                            st->done = 1;
-                        } else if (st->profile) {
-                            // timing run: keep going
-                        } else if (!isfinite(t1)) {
-                            st->done = 1;
-                            st->status = 1;
-                        } else if (t1 <= st->rr_stop) {
-                            st->done = 1;
-                            st->status = 0;
-                        } else if (st->iter >= st->max_iter) {
-                            st->done = 1;
-                            st->status = 2;
-                        }
+                        e->partials[nit + 2 * li] = t0;
+                        e->partials[nit + 2 * li + 1] = t1;
                     }
-                    *e->cnt = 0u;
-                    __threadfence();
                 }
             }
         }
     }
+    // this thread's item partials are visible device-wide before the block
+    // counts itself done
+    __threadfence();
     __syncthreads();
     // a device-side wait gave up: stop every system of the table
     if (s_abort && threadIdx.x == 0 && MODE != MODE_A) {
@@ -605,13 +630,115 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             atomicExch(&tab[q].st->done, 1);
         }
     }
-    // the last block to leave resets the work counter for the next launch
+    // the last block to leave finishes every system's reductions and resets
+    // the work counters for the next launch
+    __shared__ int s_lastblk;
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
-            queue[0] = 0u;
-            queue[1] = 0u;
-            __threadfence();
+        s_lastblk = atomicAdd(queue + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_lastblk) return;
+    __threadfence();
+    if (MODE != MODE_A) {
+        // Each system's item partials are summed in an order fixed by its
+        // item count only: systems of more than BIGSYS items by the whole
+        // block (thread t takes items t, t+NTHREADS, ... into four
+        // accumulators), smaller ones by one warp each.
+        constexpr int BIGSYS = 512;
+        __shared__ double s_red[2][NTHREADS / 32];
+        auto finish = [&](CgState *st, double t0, double t1) {
+            if (MODE == MODE_P) {
+                st->sigma = t0;
+                if (st->status == 3) {
+                    st->done = 1;
+                } else if (st->profile) {
+                    st->alpha = isfinite(t0) && t0 != 0.0 ? st->rho / t0 : 0.0;
+                } else if (!(t0 > 0.0) || !isfinite(t0)) {
+                    st->done = 1;
+                    st->status = 1;
+                } else {
+                    st->alpha = st->rho / t0;
+                }
+            } else {
+                st->beta = t0 / st->rho;
+                st->rho = t0;
+                st->rr = t1;
+                st->iter += 1;
+                st->cur ^= 1;  // the new p_old is this iteration's p
+                if (st->status == 3) {
+                    st->done = 1;
+                } else if (st->profile) {
+                    // timing run: keep going
+                } else if (!isfinite(t1)) {
+                    st->done = 1;
+                    st->status = 1;
+                } else if (t1 <= st->rr_stop) {
+                    st->done = 1;
+                    st->status = 0;
+                } else if (st->iter >= st->max_iter) {
+                    st->done = 1;
+                    st->status = 2;
+                }
+            }
+        };
+        auto item_sums = [&](const SysEntry *e, int first, int stride, double &t0, double &t1) {
+            const int nit = e->nitems;
+            double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+            int r = 0;
+            for (int i = first; i < nit; i += stride, r = (r + 1) & 3) {
+                if (MODE == MODE_P) {
+                    a[r] += __ldcg(e->partials + i);
+                } else {
+                    a[r] += __ldcg(e->partials + nit + 2 * i);
+                    b[r] += __ldcg(e->partials + nit + 2 * i + 1);
+                }
+            }
+            t0 = (a[0] + a[1]) + (a[2] + a[3]);
+            t1 = (b[0] + b[1]) + (b[2] + b[3]);
+        };
+        // large systems: the whole block, one after the other
+        for (int q = 0; q < nsys; ++q) {
+            const SysEntry *e = tab + q;
+            const int nit = e->nitems;
+            if (nit <= BIGSYS || *(volatile int *)&e->st->done) continue;
+            double t0, t1;
+            item_sums(e, threadIdx.x, NTHREADS, t0, t1);
+            t0 = warp_sum_d(t0);
+            t1 = warp_sum_d(t1);
+            if (lane == 0) {
+                s_red[0][w] = t0;
+                s_red[1][w] = t1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double u0 = 0.0, u1 = 0.0;
+                for (int r = 0; r < NTHREADS / 32; ++r) {
+                    u0 += s_red[0][r];
+                    u1 += s_red[1][r];
+                }
+                finish(e->st, u0, u1);
+            }
+            __syncthreads();
         }
+        // small systems: one warp each
+        for (int q = w; q < nsys; q += NTHREADS / 32) {
+            const SysEntry *e = tab + q;
+            const int nit = e->nitems;
+            CgState *st = e->st;
+            // systems that were done at launch (or stopped by an abort) have no partials
+            if (nit == 0 || nit > BIGSYS || *(volatile int *)&st->done) continue;
+            double t0, t1;
+            item_sums(e, lane, 32, t0, t1);
+            t0 = warp_sum_d(t0);
+            t1 = warp_sum_d(t1);
+            if (lane == 0) finish(st, t0, t1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        queue[0] = 0u;
+        queue[1] = 0u;
+        __threadfence();
     }
 }
