@@ -960,10 +960,7 @@ struct OctArgs {
     const double *tr_diag;
     long long ntr;
     CgState *st;
-    double *partials;    // pure kernels: per-block slots
-    double *tpart;       // totals of the transition kernels
-    double *tpartials;   // transition kernels: per-block slots
-    unsigned int *tcount;
+    double *partials;    // per-block slots of the dot products
 };
 
 template <int NT>
@@ -1158,7 +1155,6 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
             const uint8_t cc = cd[k];
             const int kind = cc >> 4;
             if (kind != 0) {
-                if (MODE == OM_P && kind == 3) A.p[a] = v[k];
                 if (MODE == OM_A && kind != 3) A.y[a] = (T)0;
                 continue;
             }
@@ -1223,6 +1219,47 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
             kahan(s1, c1, bs1);
         }
     }
+    // level-transition rows (explicit CSR): each block takes a fixed
+    // contiguous range of rows, one row per thread at a time
+    if (A.ntr > 0) {
+        const long long per = (A.ntr + gridDim.x - 1) / gridDim.x;
+        const long long r0 = (long long)blockIdx.x * per;
+        const long long r1 = min(A.ntr, r0 + per);
+        for (long long r = r0 + threadIdx.x; r < r1; r += OB) {
+            const int a = A.tr_slot[r];
+            T q = 0;
+            for (long long e = A.tr_ptr[r]; e < A.tr_ptr[r + 1]; ++e) {
+                const int c = A.tr_col[e];
+                T v;
+                if (MODE == OM_P) v = A.z[c] + beta * A.pold[c];
+                else if (MODE == OM_U) v = A.p[c];
+                else v = A.xin[c];
+                q += A.tr_val[e] * v;
+            }
+            if (MODE == OM_P) {
+                const T pa = A.z[a] + beta * A.pold[a];
+                A.p[a] = pa;
+                if constexpr (sizeof(T) == 4) kahan(s0, c0, pa * q);
+                else d0 += pa * q;
+            } else if (MODE == OM_U) {
+                const T D = (T)A.tr_diag[r];
+                const T pa = A.p[a];
+                A.x[a] += alpha * pa;
+                const T zn = A.zz[a] - alpha * q / D;
+                A.zz[a] = zn;
+                const T dz = D * zn;
+                if constexpr (sizeof(T) == 4) {
+                    kahan(s0, c0, dz * zn);
+                    kahan(s1, c1, dz * dz);
+                } else {
+                    d0 += dz * zn;
+                    d1 += dz * dz;
+                }
+            } else {
+                A.y[a] = q;
+            }
+        }
+    }
     if (MODE == OM_A) return;
     if constexpr (sizeof(T) == 4) {
         d0 = (double)s0 - (double)c0;
@@ -1233,62 +1270,11 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
         if (threadIdx.x == 0) {
             CgState *s = A.st;
             if (MODE == OM_P) {
-                finalize_p(s, tot[0] + A.tpart[0]);
+                finalize_p(s, tot[0]);
             } else {
-                finalize_u(s, tot[0] + A.tpart[1], tot[1] + A.tpart[2]);
+                finalize_u(s, tot[0], tot[1]);
             }
             s->counter = 0;
-        }
-    }
-}
-
-// level-transition rows (explicit CSR), one thread per row
-template <typename T, int MODE>
-__global__ void __launch_bounds__(OT) k_oct_trans(OctArgs<T> A) {
-    if (MODE != OM_A && *(volatile int *)&A.st->done) return;
-    T beta = 0, alpha = 0;
-    if (MODE == OM_P) beta = (T)A.st->beta;
-    if (MODE == OM_U) alpha = (T)A.st->alpha;
-    double acc0 = 0.0, acc1 = 0.0;
-    const long long r = blockIdx.x * (long long)OT + threadIdx.x;
-    if (r < A.ntr) {
-        const long long a = A.tr_slot[r];
-        T q = 0;
-        for (long long e = A.tr_ptr[r]; e < A.tr_ptr[r + 1]; ++e) {
-            const int c = A.tr_col[e];
-            T v;
-            if (MODE == OM_P) v = A.z[c] + beta * A.pold[c];
-            else if (MODE == OM_U) v = A.p[c];
-            else v = A.xin[c];
-            q += A.tr_val[e] * v;
-        }
-        if (MODE == OM_P) {
-            const T pa = A.z[a] + beta * A.pold[a];
-            acc0 = (double)pa * (double)q;
-        } else if (MODE == OM_U) {
-            const T D = (T)A.tr_diag[r];
-            const T pa = A.p[a];
-            A.x[a] += alpha * pa;
-            const T zn = A.zz[a] - alpha * q / D;
-            A.zz[a] = zn;
-            const double dz = (double)D * (double)zn;
-            acc0 = dz * (double)zn;
-            acc1 = dz * dz;
-        } else {
-            A.y[a] = q;
-        }
-    }
-    if (MODE == OM_A) return;
-    double mine[2] = {acc0, acc1}, tot[2];
-    if (olast_total<OT, 2>(A.tcount, A.tpartials, mine, tot)) {
-        if (threadIdx.x == 0) {
-            if (MODE == OM_P) {
-                A.tpart[0] = tot[0];
-            } else {
-                A.tpart[1] = tot[0];
-                A.tpart[2] = tot[1];
-            }
-            *A.tcount = 0;
         }
     }
 }
@@ -1917,9 +1903,6 @@ OctArgs<T> oct_args(pb_system *sys) {
     A.ntr = os->ntr;
     A.st = sys->st;
     A.partials = sys->partials;
-    A.tpart = os->tpart;
-    A.tpartials = os->partials;
-    A.tcount = os->tcount;
     return A;
 }
 
@@ -1930,11 +1913,9 @@ void oct_iteration(pb_system *sys, OctArgs<T> A, T *z, T *pold, T *p, T *x, cuda
     A.p = p;
     A.x = x;
     A.zz = z;
-    if (A.ntr > 0) k_oct_trans<T, OM_P><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
     k_oct_pure<T, OM_P><<<pure_grid<T, OM_P>(), OB, 0, s>>>(A);
-    if (A.ntr > 0) k_oct_trans<T, OM_U><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
     k_oct_pure<T, OM_U><<<pure_grid<T, OM_U>(), OB, 0, s>>>(A);
-    note_launch(A.ntr > 0 ? 4 : 2);
+    note_launch(2);
 }
 
 pb_status oct_ensure_ws(pb_system *sys, int precision, cudaStream_t s) {
@@ -2202,20 +2183,12 @@ pb_status oct_apply(pb_system *sys, int precision, const void *x, void *y, cudaS
         A.y = (float *)y;
         k_oct_pure<float, OM_A><<<pure_grid<float, OM_A>(), OB, 0, s>>>(A);
         PB_LAUNCH_CHECK();
-        if (A.ntr > 0) {
-            k_oct_trans<float, OM_A><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
-            PB_LAUNCH_CHECK();
-        }
     } else {
         OctArgs<double> A = oct_args<double>(sys);
         A.xin = (const double *)x;
         A.y = (double *)y;
         k_oct_pure<double, OM_A><<<pure_grid<double, OM_A>(), OB, 0, s>>>(A);
         PB_LAUNCH_CHECK();
-        if (A.ntr > 0) {
-            k_oct_trans<double, OM_A><<<cdiv(A.ntr, OT), OT, 0, s>>>(A);
-            PB_LAUNCH_CHECK();
-        }
     }
     (void)t;
     return PB_OK;
