@@ -279,7 +279,8 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
  * PCG iterations (the CG solve of Eq. matrixequation, Sec. 4, with FP32
  * inner iterations and FP64 iterative refinement).  A system submitted while others run joins at the
  * next replay once a slot is free; a finished one leaves at once and is
- * reported through pb_engine_wait.  The paper solves one system at a time:
+ * reported through pb_engine_wait.  Octree systems run their brick
+ * kernels beside the table, the same number of iterations per replay.  The paper solves one system at a time:
  * the engine is the serving form of the same solve, and a system's result is
  * the same (bit for bit, for the same z-chunk) alone or in any mix.
  * ------------------------------------------------------------------- */

@@ -636,10 +636,6 @@ pb_status pb_engine_submit(pb_engine *e, pb_system *s, void *stream, int64_t *ti
         set_error("pb_engine_submit: NULL argument");
         return PB_ERR_ARG;
     }
-    if (s->g->is_oct) {
-        set_error("pb_engine_submit: octree systems are solved by pb_solve");
-        return PB_ERR_UNIMPL;
-    }
     DeviceGuard dg(s->g->device);
     long long t = 0;
     pb_status rc = engine_submit(e, s, (cudaStream_t)stream, &t);

@@ -115,6 +115,8 @@ struct EngineJob {
     long long ticket = 0;
     cudaEvent_t ready = nullptr;  // recorded on the submitting stream
     int kc = 8;
+    bool oct = false;             // octree system: brick kernels beside the table
+    long long dof = 0;
     double t_submit = 0.0;
 };
 
@@ -186,7 +188,7 @@ bool engine_install(Engine *e, int q) {
     ENG_TRY(cudaMemsetAsync(e->dslots + q, 0, sizeof(EngineSlot), e->cs), "slot reset");
     ENG_TRY(cudaMemcpyAsync(sys->phi, sys->bc, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, e->cs),
             "initial iterate");
-    if (residual(sys, true, e->cs) != PB_OK) {
+    if ((hs.job.oct ? oct_engine_residual(sys, e->cs) : residual(sys, true, e->cs)) != PB_OK) {
         engine_fail(e, "initial residual", cudaGetLastError());
         return false;
     }
@@ -205,9 +207,16 @@ bool engine_refine(Engine *e, int q) {
     HostSlot &hs = e->slots[q];
     pb_system *sys = hs.job.sys;
     const GridGeo &g = sys->g->geo;
-    k_promote<float><<<cdiv(g.N, 256), 256, 0, e->cs>>>(sys->phi, sys->d32, g, sys->pad);
-    ENG_TRY(cudaGetLastError(), "promotion launch");
-    if (residual(sys, true, e->cs) != PB_OK) {
+    if (hs.job.oct) {
+        if (oct_engine_promote(sys, e->cs) != PB_OK) {
+            engine_fail(e, "promotion", cudaGetLastError());
+            return false;
+        }
+    } else {
+        k_promote<float><<<cdiv(g.N, 256), 256, 0, e->cs>>>(sys->phi, sys->d32, g, sys->pad);
+        ENG_TRY(cudaGetLastError(), "promotion launch");
+    }
+    if ((hs.job.oct ? oct_engine_residual(sys, e->cs) : residual(sys, true, e->cs)) != PB_OK) {
         engine_fail(e, "true residual", cudaGetLastError());
         return false;
     }
@@ -232,10 +241,10 @@ bool engine_upload_table(Engine *e) {
     for (int q = 0; q < e->cap; ++q) {
         tma::SysEntry &en = h[q];
         const HostSlot &hs = e->slots[q];
-        if (hs.used) {
+        if (hs.used && !hs.job.oct) {
             en = ((TmaState *)hs.job.sys->tma)->host;
             tma_entry_geometry(en, hs.job.sys->pad, hs.job.kc);
-        } else {
+        } else {  // free slot, or an octree system (solved beside the table)
             memset(&en, 0, sizeof(en));
             en.nitems = 0;
         }
@@ -271,9 +280,9 @@ void engine_complete(Engine *e, int q, const EngineSlot &m) {
     r.stats.status = m.ctl.status;
     r.stats.iters_inner = m.ctl.iters;
     r.stats.iters_outer = m.ctl.outer;
-    r.stats.kc = hs.job.kc + 1000;
+    r.stats.kc = hs.job.oct ? 0 : hs.job.kc + 1000;
     r.stats.true_rel_res = m.ctl.fn2 > 0.0 ? sqrt(m.ctl.res2 / m.ctl.fn2) : 0.0;
-    r.stats.dof = (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+    r.stats.dof = hs.job.dof;
     r.stats.model_bytes = (long long)m.ctl.iters * r.stats.dof * (8 * 4 + 2) +
                           (long long)m.ctl.outer * g.N * 64;
     r.t_submit = hs.job.t_submit;
@@ -291,6 +300,15 @@ void engine_complete(Engine *e, int q, const EngineSlot &m) {
 bool engine_issue(Engine *e, int mb) {
     ENG_TRY(cudaGraphLaunch(e->exec, e->cs), "replay");
     note_launch(2 * e->chunk);
+    // octree systems: the same number of iterations with their brick kernels
+    for (int q = 0; q < e->cap; ++q) {
+        const HostSlot &hs = e->slots[q];
+        if (!hs.used || !hs.job.oct) continue;
+        if (oct_engine_iterations(hs.job.sys, e->chunk, e->cs) != PB_OK) {
+            engine_fail(e, "octree iterations", cudaGetLastError());
+            return false;
+        }
+    }
     ENG_TRY(cudaMemcpyAsync(e->hmirror + (size_t)mb * e->cap, e->dslots, sizeof(EngineSlot) * e->cap,
                             cudaMemcpyDeviceToHost, e->cs),
             "state mirror");
@@ -494,14 +512,23 @@ pb_status engine_submit(pb_engine *eh, pb_system *sys, cudaStream_t s, long long
         set_error("the system lives on device %d, the engine on device %d", sys->g->device, e->device);
         return PB_ERR_ARG;
     }
-    pb_status rc = ensure_solver_ws(sys, PB_MIXED, s);
-    if (rc != PB_OK) return rc;
-    if ((rc = build_tma_state(sys)) != PB_OK) return rc;
-    Tuning tune;
-    if ((rc = autotune(sys, PB_MIXED, s, &tune)) != PB_OK) return rc;
     EngineJob j;
     j.sys = sys;
-    j.kc = tune.variant == 1 ? std::max(tune.kc, 4) : 8;
+    pb_status rc = PB_OK;
+    if (sys->g->is_oct) {
+        if ((rc = oct_engine_prepare(sys, s)) != PB_OK) return rc;
+        j.oct = true;
+        j.kc = 0;
+        j.dof = sys->os->nunk;
+    } else {
+        if ((rc = ensure_solver_ws(sys, PB_MIXED, s)) != PB_OK) return rc;
+        if ((rc = build_tma_state(sys)) != PB_OK) return rc;
+        Tuning tune;
+        if ((rc = autotune(sys, PB_MIXED, s, &tune)) != PB_OK) return rc;
+        j.kc = tune.variant == 1 ? std::max(tune.kc, 4) : 8;
+        const GridGeo &gg = sys->g->geo;
+        j.dof = (long long)(gg.nx - 2) * (gg.ny - 2) * (gg.nz - 2);
+    }
     j.t_submit = now_s();
     PB_CUDA_TRY(cudaEventCreateWithFlags(&j.ready, cudaEventDisableTiming));
     cudaError_t ce = cudaEventRecord(j.ready, s);

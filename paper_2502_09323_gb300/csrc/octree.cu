@@ -1852,6 +1852,18 @@ pb_status oct_assemble(pb_system *sys, cudaStream_t s) {
         return PB_ERR_ARG;
     }
     os->nnz = nnz;
+    {
+        unsigned long long *c = (unsigned long long *)dalloc(sizeof(unsigned long long), s);
+        if (!c) return PB_ERR_OOM;
+        PB_CUDA_TRY(cudaMemsetAsync(c, 0, sizeof(unsigned long long), s));
+        k_count_flags<<<num_sms() * 4, OT, 0, s>>>(t.okind, N, 0, c);
+        PB_LAUNCH_CHECK();
+        unsigned long long h0 = 0;
+        PB_CUDA_TRY(cudaMemcpyAsync(&h0, c, sizeof(h0), cudaMemcpyDeviceToHost, s));
+        PB_CUDA_TRY(cudaStreamSynchronize(s));
+        dfree(c, s);
+        os->nunk = (long long)h0 + ntr;
+    }
     const long long nnz1 = nnz > 0 ? nnz : 1;
     os->tr_col = (int *)dalloc(sizeof(int) * nnz1, s);
     os->tr_val = (double *)dalloc(sizeof(double) * nnz1, s);
@@ -2150,20 +2162,7 @@ pb_status oct_solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_s
         stats->kc = 0;
         stats->true_rel_res = fn2 > 0.0 ? sqrt(res2 / fn2) : 0.0;
         stats->seconds = wall_s() - t_start;
-        long long dof = 0;
-        // unknowns: pure and level-transition rows (counted once per build)
-        {
-            unsigned long long *c = (unsigned long long *)dalloc(sizeof(unsigned long long), s);
-            if (c) {
-                cudaMemsetAsync(c, 0, sizeof(unsigned long long), s);
-                k_count_flags<<<num_sms() * 4, OT, 0, s>>>(t.okind, N, 0, c);
-                unsigned long long h0 = 0;
-                cudaMemcpyAsync(&h0, c, sizeof(h0), cudaMemcpyDeviceToHost, s);
-                cudaStreamSynchronize(s);
-                dof = (long long)h0 + sys->os->ntr;
-                dfree(c, s);
-            }
-        }
+        const long long dof = sys->os->nunk;
         stats->dof = dof;
         const long long per = o->precision == PB_MIXED ? (8 * 4 + 2) : (8 * 8 + 6 * 8 + 2);
         stats->model_bytes = (long long)iters * dof * per + (long long)outer * N * 64;
@@ -2237,6 +2236,38 @@ pb_status oct_energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out) {
     PB_CUDA_TRY(cudaStreamSynchronize(s));
     dfree(partials, s);
     *out = *sys->h_energy;
+    return PB_OK;
+}
+
+}  // namespace pbg
+
+// ------------------------------------------------ serving-engine hooks ---
+// The continuous-batching engine runs octree systems beside its launch
+// table: these queue one system's pieces on the engine's stream (the
+// system's CG state pointer is the engine slot's).
+namespace pbg {
+
+pb_status oct_engine_prepare(pb_system *sys, cudaStream_t s) { return oct_ensure_ws(sys, PB_MIXED, s); }
+
+pb_status oct_engine_residual(pb_system *sys, cudaStream_t s) { return oct_residual(sys, true, s); }
+
+// promotion of the FP32 correction and the hanging values of phi
+pb_status oct_engine_promote(pb_system *sys, cudaStream_t s) {
+    const OctDev &t = sys->g->ot;
+    k_oct_promote<float><<<cdiv(t.N, OT), OT, 0, s>>>(t, sys->phi, sys->d32);
+    PB_LAUNCH_CHECK();
+    k_oct_hang<<<cdiv(t.N, OT), OT, 0, s>>>(t, bc_desc(sys), sys->phi);
+    PB_LAUNCH_CHECK();
+    return PB_OK;
+}
+
+// n (even) FP32 PCG iterations starting from direction parity 0; the
+// kernels do nothing once the state says done
+pb_status oct_engine_iterations(pb_system *sys, int n, cudaStream_t s) {
+    OctArgs<float> A = oct_args<float>(sys);
+    float *bufs[2] = {sys->pa32, sys->pb32};
+    for (int c = 0; c < n; ++c) oct_iteration<float>(sys, A, sys->z32, bufs[c & 1], bufs[(c & 1) ^ 1], sys->d32, s);
+    PB_CUDA_TRY(cudaGetLastError());
     return PB_OK;
 }
 

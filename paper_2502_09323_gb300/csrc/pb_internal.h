@@ -98,6 +98,7 @@ struct OctDev {
 // Level-transition rows of an octree system: explicit CSR of P^T K P.
 struct OctSys {
     long long ntr, nnz;
+    long long nunk;       // unknowns (pure and level-transition rows)
     int *tr_slot;         // [ntr] slot of each row (increasing)
     int *tr_row;          // [N] row of each slot, -1 if none
     long long *tr_ptr;    // [ntr + 1]
@@ -241,6 +242,10 @@ pb_status oct_apply(pb_system *sys, int precision, const void *x, void *y, cudaS
 pb_status oct_energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);
 pb_status oct_fill_kappa(const pb_system *sys, double *dst, cudaStream_t s);
 pb_status oct_profile(pb_system *sys, int precision, int which, int reps, cudaStream_t s);
+pb_status oct_engine_prepare(pb_system *sys, cudaStream_t s);
+pb_status oct_engine_residual(pb_system *sys, cudaStream_t s);
+pb_status oct_engine_promote(pb_system *sys, cudaStream_t s);
+pb_status oct_engine_iterations(pb_system *sys, int n, cudaStream_t s);
 
 // ------------------------------------------------------------- energy.cu --
 pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out);

@@ -20,8 +20,8 @@ import time
 
 import numpy as np
 
-from . import (CT_PAIRS, CT_SURFACE, Engine, GridSpec, Params, SolveOpts, pb_assemble_coeffs,
-               pb_build_grid, pb_coulomb_terms, pb_energy, pb_get_phi)
+from . import (CT_PAIRS, CT_SURFACE, Engine, GridSpec, OctreeSpec, Params, SolveOpts,
+               pb_assemble_coeffs, pb_build_grid, pb_coulomb_terms, pb_energy, pb_get_phi)
 
 # nodes per axis offered to uniform serving grids (32k + 1)
 GRID_SIZES = tuple(range(65, 2049, 32))
@@ -50,7 +50,48 @@ def uniform_spec(atoms: np.ndarray, h: float = 0.5, fill: float = 1.5,
     return GridSpec(n=(n, n, n), origin=tuple(float(v) for v in origin), h=float(h), fill=0.0)
 
 
-def device_bytes_estimate(spec: GridSpec, n_atoms: int) -> int:
+def octree_spec(atoms: np.ndarray, h_fine: float = 0.25, h_bulk: float = 1.0,
+                refine_dist: float = 3.0, fill: float = 1.5) -> OctreeSpec:
+    """Brick octree placed automatically around the atoms."""
+    return OctreeSpec(h_fine=h_fine, h_bulk=h_bulk, refine_dist=refine_dist, fill=fill)
+
+
+# octree: device bytes per node slot (the uniform set plus node kinds, inside
+# flags and the transition-row map), bytes per listed edge, and listed edges
+# per atom at 0.25 A (they scale with 1/h^2)
+OCT_BYTES_PER_SLOT = 112
+OCT_BYTES_PER_EDGE = 64
+OCT_EDGES_PER_ATOM = 400
+
+
+def _octree_estimate(spec: OctreeSpec, atoms: np.ndarray) -> int:
+    lo = (atoms[:, :3] - atoms[:, 3:4]).min(axis=0)
+    hi = (atoms[:, :3] + atoms[:, 3:4]).max(axis=0)
+    c = 0.5 * (lo + hi)
+    extent = float((hi - lo).max())
+    n0 = max(1, math.ceil(spec.fill * extent / (8.0 * spec.h_bulk)))
+    side = n0 * 8.0 * spec.h_bulk
+    reach = float(np.max(np.linalg.norm(atoms[:, :3] - c, axis=1) + atoms[:, 3]))
+    levels = int(round(math.log2(spec.h_bulk / spec.h_fine)))
+    slots = 0.0
+    r = reach + spec.refine_dist
+    h = spec.h_fine
+    for _ in range(levels):
+        # each level's region grows by two of its bricks (brick rounding, balance)
+        r += 16.0 * h
+        slots += 4.0 / 3.0 * math.pi * r ** 3 / h ** 3
+        h *= 2.0
+    slots += (side / spec.h_bulk) ** 3
+    edges = OCT_EDGES_PER_ATOM * len(atoms) * (0.25 / spec.h_fine) ** 2
+    # the build classifies the whole domain on the finest lattice (freed after)
+    transient = 6.0 * (side / spec.h_fine + 1) ** 3
+    return int(OCT_BYTES_PER_SLOT * slots + OCT_BYTES_PER_EDGE * edges + transient) + FIXED_BYTES
+
+
+def device_bytes_estimate(spec, n_atoms: int, atoms: np.ndarray | None = None) -> int:
+    """Device memory of one request's system (octree specs need the atoms)."""
+    if isinstance(spec, OctreeSpec):
+        return _octree_estimate(spec, atoms)
     nx, ny, nz = spec.n
     sx = (nx + 15) // 16 * 16  # FP32 rows are padded to 16 elements
     return BYTES_PER_NODE * sx * ny * nz + 64 * n_atoms + FIXED_BYTES
@@ -69,12 +110,16 @@ class Server:
 
     def __init__(self, capacity: int = 64, hbm_budget_bytes: float = 150e9,
                  params: Params | None = None, opts: SolveOpts | None = None, h: float = 0.5,
-                 fill: float = 1.5, energy: bool = True, keep_phi: bool = False):
+                 fill: float = 1.5, energy: bool = True, keep_phi: bool = False,
+                 grid: str = "uniform"):
         import torch
         self.torch = torch
         self.params = params or Params()
         self.opts = opts or SolveOpts()
         self.h, self.fill = h, fill
+        if grid not in ("uniform", "octree"):
+            raise ValueError("grid must be 'uniform' or 'octree'")
+        self.grid = grid
         self.energy = energy
         self.keep_phi = keep_phi
         self.budget = float(hbm_budget_bytes)
@@ -92,9 +137,16 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
+    def spec_for(self, atoms: np.ndarray):
+        """The request's grid: uniform of spacing h, or a brick octree whose
+        finest spacing is h."""
+        if getattr(self, "grid", "uniform") == "octree":
+            return octree_spec(atoms, h_fine=self.h, fill=self.fill)
+        return uniform_spec(atoms, self.h, self.fill)
+
     def _admit(self, req: Request, rec: dict):
-        spec = req.spec or uniform_spec(req.atoms, self.h, self.fill)
-        rec["n"] = spec.n[0]
+        spec = req.spec or self.spec_for(req.atoms)
+        rec["n"] = spec.n[0] if isinstance(spec, GridSpec) else 0
         with self.torch.cuda.stream(self.stream):
             g = pb_build_grid(spec, req.atoms, self.stream)
             s = pb_assemble_coeffs(g, self.params, self.stream)
@@ -121,8 +173,8 @@ class Server:
             # admission: FIFO, while a slot is free and the budget allows
             while waiting and len(inflight) < self.capacity:
                 req = waiting[0]
-                spec = req.spec or uniform_spec(req.atoms, self.h, self.fill)
-                need = device_bytes_estimate(spec, len(req.atoms))
+                spec = req.spec or self.spec_for(req.atoms)
+                need = device_bytes_estimate(spec, len(req.atoms), req.atoms)
                 if inflight and used + need > self.budget:
                     break
                 if need > self.budget:

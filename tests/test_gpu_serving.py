@@ -181,3 +181,72 @@ def test_server_poisson_stream_budget_and_oracle_energy(pb, orc):
         torch.cuda.synchronize()
         used = torch.cuda.memory_allocated() - before
     assert used <= serving.device_bytes_estimate(spec, len(req.atoms))
+
+
+def _octree_system(pb, na, seed):
+    atoms = pb_inputs.globular_molecule(na, seed=seed)
+    g = pb.pb_build_grid(pb.OctreeSpec(h_fine=0.5, h_bulk=1.0, refine_dist=2.0, fill=1.8), atoms)
+    s = pb.pb_assemble_coeffs(g, pb.Params(bc=pb.BC_DH))
+    pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+    return s
+
+
+def test_engine_octree_beside_uniform_equals_pb_solve(pb, reference):
+    """Octree systems are served beside uniform ones (their brick kernels run
+    with every replay); each keeps the bits of its pb_solve."""
+    oshapes = [(150, 401), (260, 402)]
+    oref = []
+    for na, seed in oshapes:
+        s = _octree_system(pb, na, seed)
+        st = pb.pb_solve(s, pb.SolveOpts(precision=pb.MIXED, **OPTS))
+        assert st["status"] == 0
+        oref.append((pb.pb_get_phi(s), st, pb.pb_energy(s)))
+    with pb.Engine(capacity=3, opts=pb.SolveOpts(precision=pb.MIXED, **OPTS)) as eng:
+        systems = {}
+        for i, (na, seed) in enumerate(oshapes):
+            systems[eng.submit(_octree_system(pb, na, seed))] = ("oct", i)
+        for i in (1, 3):
+            systems[eng.submit(_system(pb, *SHAPES[i]))] = ("uni", i)
+        got = _drain(eng, 4)
+    for r in got:
+        kind, i = systems[r["ticket"]]
+        phi, st_ref, e_ref = oref[i] if kind == "oct" else reference[i]
+        assert r["stats"]["status"] == 0
+        assert r["stats"]["iters_inner"] == st_ref["iters_inner"]
+        assert r["stats"]["dof"] == st_ref["dof"]
+        assert np.array_equal(pb.pb_get_phi(r["system"]), phi), (kind, i)
+        assert pb.pb_energy(r["system"]) == e_ref
+
+
+def test_server_octree_stream_within_budget(pb):
+    import torch
+    from paper_2502_09323_gb300 import serving
+    sizes = pb_inputs.batch_sizes(6, 5100, 60, 400)
+    arrivals = pb_inputs.poisson_arrivals(6, rate_hz=50.0, seed=5100)
+    reqs = [serving.Request(rid=j, atoms=pb_inputs.globular_molecule(int(n), seed=5101 + j),
+                            arrival_s=float(t)) for j, (n, t) in enumerate(zip(sizes, arrivals))]
+    srv_kw = dict(h=0.5, grid="octree")
+    need = [serving.device_bytes_estimate(serving.octree_spec(r.atoms, h_fine=0.5), len(r.atoms),
+                                          r.atoms) for r in reqs]
+    budget = 2.5 * max(need)
+    opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-8)
+    with serving.Server(capacity=4, hbm_budget_bytes=budget, opts=opts, **srv_kw) as srv:
+        recs = srv.run(reqs)
+        assert srv.max_used <= budget
+    assert len(recs) == 6
+    for r in recs:
+        assert r["stats"]["status"] == 0 and r["stats"]["true_rel_res"] <= 1e-8
+        assert r["energy"]["e_total"] != 0.0
+    # the estimate covers the peak of one request (its build included)
+    big = max(reqs, key=lambda r: len(r.atoms))
+    spec = serving.octree_spec(big.atoms, h_fine=0.5)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    g = pb.pb_build_grid(spec, big.atoms)
+    s = pb.pb_assemble_coeffs(g, pb.Params())
+    pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+    pb.pb_solve(s, opts)
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated() - base
+    assert peak <= serving.device_bytes_estimate(spec, len(big.atoms), big.atoms)
