@@ -59,9 +59,13 @@ def parse():
     ap.add_argument("--no-octree", action="store_true")
     ap.add_argument("--octree-only", action="store_true",
                     help="run only the octree workload (for profiling)")
+    ap.add_argument("--octree-atoms", type=int, default=20000,
+                    help="atoms of the octree workload (smaller for profiling captures)")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-rate", type=float, default=6.0)
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=None,
+                    help="Poisson arrival rate (default 1.5/s on octree grids, 6/s on uniform)")
+    ap.add_argument("--serve-grid", default="octree", choices=["octree", "uniform"])
     ap.add_argument("--tuning", default=None,
                     help="VARIANT:ZCHUNK for the FP32 PCG kernels instead of the autotuner "
                          "(e.g. 1:0 = TMA-staged persistent); for profiler runs")
@@ -308,7 +312,11 @@ def run_octree(args, pb, pb_inputs, torch, steps=3, warmup=1, fp64=True):
     path per step (build, coefficients, Coulomb terms, mixed solve to 1e-8,
     energy), and the plain FP64 solve of the same system."""
     import numpy as np
-    wl = OCTREE
+    wl = dict(OCTREE)
+    if args.octree_atoms != wl["n_atoms"]:
+        # same density: the ball radius scales with the cube root of the count
+        wl["radius"] = wl["radius"] * (args.octree_atoms / wl["n_atoms"]) ** (1.0 / 3.0)
+        wl["n_atoms"] = args.octree_atoms
     atoms = pb_inputs.globular_molecule(wl["n_atoms"], seed=wl["seed"], radius=wl["radius"])
     atoms_dev = torch.tensor(atoms, device="cuda")
     spec = pb.OctreeSpec(h_fine=wl["h_fine"], h_bulk=wl["h_bulk"], refine_dist=wl["refine_dist"],
@@ -386,17 +394,22 @@ def run_octree(args, pb, pb_inputs, torch, steps=3, warmup=1, fp64=True):
 def run_serving(args, pb, pb_inputs, torch):
     """Poisson stream of solves (atom counts log-uniform in [300, 50000],
     arrivals and counts seeded 5000, molecule j seeded 5000 + j) served with
-    continuous batching under a 150 GB device-memory budget; uniform grids of
-    spacing 0.5 A stand in for the 0.25 A octree."""
+    continuous batching under a 150 GB device-memory budget, on brick octrees
+    of 0.25 A finest spacing (1 A bulk, refined within 3 A of the atom
+    spheres), or on uniform grids of spacing 0.5 A."""
     from paper_2502_09323_gb300 import serving
     count = args.serve_requests
+    octree = args.serve_grid == "octree"
+    rate = args.serve_rate if args.serve_rate else (1.5 if octree else 6.0)
+    h = 0.25 if octree else 0.5
     sizes = pb_inputs.batch_sizes(count, 5000, 300, 50000)
-    arrivals = pb_inputs.poisson_arrivals(count, args.serve_rate, seed=5000)
+    arrivals = pb_inputs.poisson_arrivals(count, rate, seed=5000)
     reqs = [serving.Request(rid=j, atoms=pb_inputs.globular_molecule(int(n), seed=5000 + j),
                             arrival_s=float(t)) for j, (n, t) in enumerate(zip(sizes, arrivals))]
     opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-8)
-    # warm-up: the autotuner sees every grid shape of the stream once
-    shapes = sorted({serving.uniform_spec(r.atoms, h=0.5).n[0] for r in reqs})
+    # warm-up: uniform grids let the autotuner see every grid shape of the
+    # stream once; octree grids run one small solve through the engine
+    shapes = [] if octree else sorted({serving.uniform_spec(r.atoms, h=h).n[0] for r in reqs})
     with pb.Engine(capacity=4, opts=opts) as eng:
         for n in shapes:
             one = pb_inputs.globular_molecule(40, seed=n)
@@ -407,9 +420,18 @@ def run_serving(args, pb, pb_inputs, torch):
             while not eng.wait(timeout_s=0.1):
                 pass
             del s, g
+        if octree:
+            one = pb_inputs.globular_molecule(300, seed=4999)
+            g = pb.pb_build_grid(serving.octree_spec(one, h_fine=h), one)
+            s = pb.pb_assemble_coeffs(g, pb.Params())
+            eng.submit(s)
+            while not eng.wait(timeout_s=0.1):
+                pass
+            del s, g
     torch.cuda.synchronize()
     launches0 = pb.pb_kernel_launches()
-    with serving.Server(capacity=64, hbm_budget_bytes=150e9, opts=opts, h=0.5) as srv:
+    with serving.Server(capacity=64, hbm_budget_bytes=150e9, opts=opts, h=h,
+                        grid=args.serve_grid) as srv:
         recs = srv.run(reqs)
         max_used = srv.max_used
     launches = pb.pb_kernel_launches() - launches0
@@ -424,14 +446,16 @@ def run_serving(args, pb, pb_inputs, torch):
     em = next(r for r in recs if r["rid"] == small.rid)["energy"]["e_total"]
     dofs = [r["stats"]["dof"] for r in recs]
     out = {
-        "workload": f"{count} requests, Poisson arrivals at {args.serve_rate:g}/s (seed 5000), "
-                    "globular molecules with atoms log-uniform [300, 50000], uniform grids "
-                    "h = 0.5 A (32k+1 nodes per axis, fill 1.5) standing in for the 0.25 A octree, "
-                    "mixed precision to 1e-8, 150 GB budget, 64 slots",
-        "rate_hz": args.serve_rate, **summ,
+        "workload": f"{count} requests, Poisson arrivals at {rate:g}/s (seed 5000), "
+                    "globular molecules with atoms log-uniform [300, 50000], "
+                    + ("brick octrees h 0.25..1 A refined within 3 A of the atom spheres"
+                       if octree else "uniform grids h = 0.5 A (32k+1 nodes per axis)")
+                    + ", fill 1.5, mixed precision to 1e-8, 150 GB budget, 64 slots",
+        "grid": args.serve_grid,
+        "rate_hz": rate, **summ,
         "engine_mean_ms": 1e3 * statistics.mean(r["engine_s"] for r in recs),
         "max_budget_used_gb": max_used / 1e9,
-        "grid_sizes": sorted({r["n"] for r in recs}),
+        "dof_max": int(max(dofs)),
         "dof_total": int(sum(dofs)),
         "all_converged": all(r["stats"]["status"] == 0 for r in recs),
         "true_rel_res_max": max(r["stats"]["true_rel_res"] for r in recs),
