@@ -141,7 +141,6 @@ void pb_grid_free(pb_grid *g) {
     cudaStreamSynchronize(s);
     dfree(g->atoms, s);
     dfree(g->inside, s);
-    dfree(g->near_, s);
     dfree(g->cells.start, s);
     dfree(g->cells.atom, s);
     dfree(g->cid, s);

@@ -141,25 +141,23 @@ k_prep(const double *__restrict__ atoms, long long na, int auto_place, int nmax,
 }
 
 // --------------------------------------------------------- classification --
-// Node a is inside when (dx*dx + dy*dy) + dz*dz < R*R for some atom; "near"
-// marks nodes within R + 1.01 h of a centre: an edge that meets a ball has its
-// low node within R + h of that ball's centre, so only edges with a near low
-// node need the interval test.
+// Node a is inside when (dx*dx + dy*dy) + dz*dz < R*R for some atom.  One
+// block per atom over the nodes of the ball's bounding box (one node of
+// margin on each side).
 __global__ void k_classify(const double *__restrict__ atoms, long long na, GridGeo g,
-                           uint8_t *__restrict__ inside, uint8_t *__restrict__ nearf) {
+                           uint8_t *__restrict__ inside) {
     const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
     int nn[3] = {g.nx, g.ny, g.nz};
     for (long long at = blockIdx.x; at < na; at += gridDim.x) {
         double c[3] = {X[at], Y[at], Z[at]};
         double r = R[at];
-        double rn = r + 1.01 * g.h;
         long long lo[3], hi[3], ext[3];
         for (int d = 0; d < 3; ++d) {
-            lo[d] = clampll((long long)floor((c[d] - rn - g.o[d]) / g.h) - 1, 0, nn[d] - 1);
-            hi[d] = clampll((long long)ceil((c[d] + rn - g.o[d]) / g.h) + 1, 0, nn[d] - 1);
+            lo[d] = clampll((long long)floor((c[d] - r - g.o[d]) / g.h) - 1, 0, nn[d] - 1);
+            hi[d] = clampll((long long)ceil((c[d] + r - g.o[d]) / g.h) + 1, 0, nn[d] - 1);
             ext[d] = hi[d] - lo[d] + 1;
         }
-        double R2 = r * r, Rn2 = rn * rn;
+        double R2 = r * r;
         long long tot = ext[0] * ext[1] * ext[2];
         for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
             long long i = lo[0] + t % ext[0];
@@ -169,9 +167,7 @@ __global__ void k_classify(const double *__restrict__ atoms, long long na, GridG
             double dy = node_coord(g, 1, j) - c[1];
             double dz = node_coord(g, 2, k) - c[2];
             double d2 = (dx * dx + dy * dy) + dz * dz;
-            long long a = (k * g.ny + j) * g.nx + i;
-            if (d2 < Rn2) nearf[a] = 1;
-            if (d2 < R2) inside[a] = 1;
+            if (d2 < R2) inside[(k * g.ny + j) * g.nx + i] = 1;
         }
     }
 }
@@ -251,7 +247,7 @@ __global__ void k_cell_sort(const int *__restrict__ start, int *__restrict__ lis
 // ------------------------------------------------------- inside fraction --
 // Interval of the edge (x_a, x_a + h e_d) inside one ball, parameter t in
 // [0,1]: (u_d + t h)^2 = R^2 - |u_perp|^2 with u = x_a - c.
-__device__ __forceinline__ bool ball_interval(const double xa[3], int d, double h, double cx,
+__device__ __noinline__ bool ball_interval(const double xa[3], int d, double h, double cx,
                                               double cy, double cz, double R, double &t0,
                                               double &t1) {
     double c[3] = {cx, cy, cz};
@@ -349,30 +345,155 @@ __device__ __forceinline__ EdgeRef edge_ref(const GridGeo &g, long long e) {
     return r;
 }
 
-// flag[e] = 1 when edge e is listed: 0 < alpha < 1 or endpoints differ.
-__global__ void k_edge_flags(const double *__restrict__ atoms, long long na, GridGeo g,
-                             CellList cl, const int *__restrict__ cstart,
-                             const int *__restrict__ clist, const uint8_t *__restrict__ inside,
-                             const uint8_t *__restrict__ nearf, uint8_t *__restrict__ flags,
-                             long long nflags, BuildInfo *info) {
-    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= nflags) return;
-    uint8_t fl = 0;
-    if (e < 3 * g.N) {
-        EdgeRef r = edge_ref(g, e);
-        int nn[3] = {g.nx, g.ny, g.nz};
-        if (r.ijk[r.d] < nn[r.d] - 1 && nearf[r.a]) {
-            double xa[3] = {node_coord(g, 0, r.ijk[0]), node_coord(g, 1, r.ijk[1]),
-                            node_coord(g, 2, r.ijk[2])};
-            double al;
-            if (!edge_alpha(atoms, na, cl, cstart, clist, xa, r.d, g.h, al)) {
-                atomicOr(&info->err, ERRF_TOO_MANY_BALLS);
-                al = 0.0;
+// Candidate edges.  An edge's inside fraction can lie strictly between 0 and
+// 1 only when some ball's interval on it is partial (t0 > 0 or t1 < 1): on
+// every other edge each interval is empty or all of [0, 1], so alpha is 0 or
+// 1 and the edge is listed exactly when its end nodes differ in `inside`.
+// One block per atom, one thread per lattice line (direction d and the node
+// indices of the two other axes) through the ball's bounding box.  Along a
+// line both a0 and a1 of ball_interval fall as the edge moves up (x_a[d]
+// enters through u_d = x_a[d] - c[d] and every rounded step after it is
+// monotone), so the scan going up stops at the first edge with t0 = 0 and the
+// scan coming down at the first with t1 = 1: every edge between the two has
+// the interval [0, 1].  Candidates get flag byte 2 (several balls may write
+// the same byte, with the same value).
+__global__ void k_edge_cand(const double *__restrict__ atoms, long long na, GridGeo g,
+                            uint8_t *__restrict__ flags) {
+    const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    const long long step[3] = {1, (long long)g.nx, (long long)g.nx * g.ny};
+    for (long long at = blockIdx.x; at < na; at += gridDim.x) {
+        const double cx = X[at], cy = Y[at], cz = Z[at], r = R[at];
+        const double c[3] = {cx, cy, cz};
+        long long lo[3], hi[3], ext[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = clampll((long long)floor((c[d] - r - g.o[d]) / g.h) - 1, 0, nn[d] - 1);
+            hi[d] = clampll((long long)ceil((c[d] + r - g.o[d]) / g.h) + 1, 0, nn[d] - 1);
+            ext[d] = hi[d] - lo[d] + 1;
+        }
+        const long long nl0 = ext[1] * ext[2], nl1 = ext[0] * ext[2], nl2 = ext[0] * ext[1];
+        for (long long t = threadIdx.x; t < nl0 + nl1 + nl2; t += blockDim.x) {
+            int d;
+            long long q;
+            if (t < nl0) {
+                d = 0;
+                q = t;
+            } else if (t < nl0 + nl1) {
+                d = 1;
+                q = t - nl0;
+            } else {
+                d = 2;
+                q = t - nl0 - nl1;
             }
-            fl = ((al > 0.0 && al < 1.0) || inside[r.a] != inside[r.b]) ? 1 : 0;
+            const int e = (d == 0) ? 1 : 0;
+            const int f = (d == 2) ? 1 : 2;
+            const long long ie = lo[e] + q % ext[e];
+            const long long jf = lo[f] + q / ext[e];
+            const long long ilo = lo[d];
+            const long long ihi = hi[d] < (long long)nn[d] - 2 ? hi[d] : (long long)nn[d] - 2;
+            if (ihi < ilo) continue;
+            double xa[3];
+            xa[e] = node_coord(g, e, ie);
+            xa[f] = node_coord(g, f, jf);
+            const long long base = (long long)d * g.N + ie * step[e] + jf * step[f];
+            long long iu = ihi + 1;
+            for (long long i = ilo; i <= ihi; ++i) {
+                xa[d] = node_coord(g, d, i);
+                double t0, t1;
+                if (!ball_interval(xa, d, g.h, cx, cy, cz, r, t0, t1)) continue;
+                if (t0 > 0.0 || t1 < 1.0) flags[base + i * step[d]] = 2;
+                if (!(t0 > 0.0)) {
+                    iu = i;
+                    break;
+                }
+            }
+            for (long long i = ihi; i > iu; --i) {
+                xa[d] = node_coord(g, d, i);
+                double t0, t1;
+                if (!ball_interval(xa, d, g.h, cx, cy, cz, r, t0, t1)) continue;
+                if (t0 > 0.0 || t1 < 1.0) flags[base + i * step[d]] = 2;
+                if (!(t1 < 1.0)) break;
+            }
         }
     }
-    flags[e] = fl;
+}
+
+// flag[e] = 1 when edge e is listed: 0 < alpha < 1 or its end nodes differ in
+// `inside`.  One block per 4096 edges: non-candidate bytes get the inside
+// test, the tile's candidates are gathered in shared memory and shared out
+// over the block for the full inside fraction (union of all balls' intervals).
+__global__ void __launch_bounds__(CHUNK_THREADS)
+k_edge_flags(const double *__restrict__ atoms, long long na, GridGeo g, CellList cl,
+             const int *__restrict__ cstart, const int *__restrict__ clist,
+             const uint8_t *__restrict__ inside, uint8_t *__restrict__ flags, BuildInfo *info) {
+    __shared__ uint4 s_fl[CHUNK_THREADS];
+    __shared__ int s_list[CHUNK_BYTES];
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const long long tile = (long long)blockIdx.x * CHUNK_BYTES;
+    uint4 v = reinterpret_cast<const uint4 *>(flags)[(long long)blockIdx.x * CHUNK_THREADS +
+                                                     threadIdx.x];
+    unsigned w[4] = {v.x, v.y, v.z, v.w};
+    // first edge of this thread's 16, then stepped node by node
+    long long e0 = tile + 16ll * threadIdx.x;
+    int d = (int)(e0 / g.N);
+    long long a = e0 - (long long)d * g.N;
+    long long i = a % g.nx, row = a / g.nx;
+    long long j = row % g.ny, k = row / g.ny;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned out = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            unsigned u = (w[q] >> (8 * b)) & 0xffu;
+            unsigned fl = 0;
+            if (d < 3) {
+                if (u == 2u) {
+                    int p = atomicAdd(&s_n, 1);
+                    s_list[p] = 16 * threadIdx.x + 4 * q + b;
+                } else {
+                    long long id = d == 0 ? i : (d == 1 ? j : k);
+                    long long nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+                    long long st = d == 0 ? 1 : (d == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+                    if (id < nd - 1 && inside[a] != inside[a + st]) fl = 1;
+                }
+            }
+            out |= fl << (8 * b);
+            ++a;
+            if (++i == g.nx) {
+                i = 0;
+                if (++j == g.ny) {
+                    j = 0;
+                    if (++k == g.nz) {
+                        k = 0;
+                        a = 0;
+                        ++d;
+                    }
+                }
+            }
+        }
+        w[q] = out;
+    }
+    s_fl[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+    __syncthreads();
+    uint8_t *sb = reinterpret_cast<uint8_t *>(s_fl);
+    const int n = s_n;
+    for (int p = threadIdx.x; p < n; p += CHUNK_THREADS) {
+        const int off = s_list[p];
+        EdgeRef r = edge_ref(g, tile + off);
+        double xa[3] = {node_coord(g, 0, r.ijk[0]), node_coord(g, 1, r.ijk[1]),
+                        node_coord(g, 2, r.ijk[2])};
+        double al;
+        if (!edge_alpha(atoms, na, cl, cstart, clist, xa, r.d, g.h, al)) {
+            atomicOr(&info->err, ERRF_TOO_MANY_BALLS);
+            al = 0.0;
+        }
+        sb[off] = ((al > 0.0 && al < 1.0) || inside[r.a] != inside[r.b]) ? 1 : 0;
+    }
+    __syncthreads();
+    reinterpret_cast<uint4 *>(flags)[(long long)blockIdx.x * CHUNK_THREADS + threadIdx.x] =
+        s_fl[threadIdx.x];
 }
 
 // ------------------------------------------------- ordered compaction --
@@ -531,13 +652,11 @@ pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
 
     // ---- classification
     g->inside = (uint8_t *)dalloc(N, s);
-    g->near_ = (uint8_t *)dalloc(N, s);
-    if (!g->inside || !g->near_) return PB_ERR_OOM;
+    if (!g->inside) return PB_ERR_OOM;
     PB_CUDA_TRY(cudaMemsetAsync(g->inside, 0, N, s));
-    PB_CUDA_TRY(cudaMemsetAsync(g->near_, 0, N, s));
+    const unsigned atom_blocks = (unsigned)(na < 65535 ? na : 65535);
     {
-        unsigned blocks = (unsigned)(na < 65535 ? na : 65535);
-        k_classify<<<blocks, 256, 0, s>>>(g->atoms, na, geo, g->inside, g->near_);
+        k_classify<<<atom_blocks, 256, 0, s>>>(g->atoms, na, geo, g->inside);
         PB_LAUNCH_CHECK();
     }
     k_count_inside<<<num_sms() * 4, 256, 0, s>>>(g->inside, N, g->d_info);
@@ -583,8 +702,14 @@ pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
     int *ccount = (int *)dalloc(sizeof(int) * (nchunks + 1), s);
     int *coffs = (int *)dalloc(sizeof(int) * (nchunks + 1), s);
     if (!flags || !ccount || !coffs) return PB_ERR_OOM;
-    k_edge_flags<<<cdiv(nflags, 256), 256, 0, s>>>(g->atoms, na, geo, cl, cl.start, cl.atom,
-                                                   g->inside, g->near_, flags, nflags, g->d_info);
+    PB_CUDA_TRY(cudaMemsetAsync(flags, 0, nflags, s));
+    if (na > 0) {
+        k_edge_cand<<<atom_blocks, 128, 0, s>>>(g->atoms, na, geo, flags);
+        PB_LAUNCH_CHECK();
+    }
+    k_edge_flags<<<(unsigned)nchunks, CHUNK_THREADS, 0, s>>>(g->atoms, na, geo, cl, cl.start,
+                                                              cl.atom, g->inside, flags,
+                                                              g->d_info);
     PB_LAUNCH_CHECK();
     k_chunk_count<<<(unsigned)nchunks, CHUNK_THREADS, 0, s>>>((const uint4 *)flags, ccount);
     PB_LAUNCH_CHECK();

@@ -1666,9 +1666,7 @@ pb_status oct_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
     }
     // the finest-lattice arrays are no longer needed
     dfree(g->inside, s);
-    dfree(g->near_, s);
     dfree(g->rowstart, s);
-    g->near_ = nullptr;
     g->rowstart = nullptr;
     g->inside = sin;
     g->ninside = (long long)hin;

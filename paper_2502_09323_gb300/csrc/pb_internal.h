@@ -121,7 +121,6 @@ struct pb_grid {
     long long na;
     double *atoms;        // SoA: x[na], y[na], z[na], R[na], q[na]
     uint8_t *inside;      // [N] 1 = solute
-    uint8_t *near_;       // [N] 1 = within R + h of some atom centre
     pbg::CellList cells;
     long long ncross, nflux, ninside;
     long long *cid;       // [ncross] edge ids, increasing

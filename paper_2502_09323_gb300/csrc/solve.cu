@@ -163,14 +163,15 @@ __device__ __forceinline__ double block_sum(double v, double *sred) {
 }
 
 // Sum partials[0..nb) (and partials[nb..2nb) when TWO) in a fixed order by the
-// last block to finish; returns true in that block (all threads).
-template <int NT, bool TWO>
+// last block to finish; returns true in that block (all threads).  With
+// REDUCED the block's own totals are already in thread 0's mine0/mine1.
+template <int NT, bool TWO, bool REDUCED = false>
 __device__ bool last_block_total(CgState *st, double *partials, int nb, double mine0,
                                  double mine1, double *sred, double &tot0, double &tot1) {
     __shared__ int s_last;
     int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    double b0 = block_sum<NT>(mine0, sred);
-    double b1 = TWO ? block_sum<NT>(mine1, sred) : 0.0;
+    double b0 = REDUCED ? mine0 : block_sum<NT>(mine0, sred);
+    double b1 = TWO ? (REDUCED ? mine1 : block_sum<NT>(mine1, sred)) : 0.0;
     if (threadIdx.x == 0) {
         partials[bid] = b0;
         if (TWO) partials[nb + bid] = b1;
@@ -498,7 +499,11 @@ k_stencil(KArgs<T> A, CP cp) {
 // FP64 true residual r = f - A phi on interior nodes (boundary neighbours
 // read their Dirichlet value through the lift already in f, so they are
 // masked here).  Writes z = r/diag to the padded solver layout (FP32 or FP64)
-// and reduces |r|^2 and r.z.
+// and reduces |r|^2 and r.z.  Persistent grid (the blocks resident on the
+// GPU): the stencil is the only FP64 arithmetic per node; for the FP32 solver
+// |r|^2 and r.z are summed in FP32 per thread and per block (they serve as
+// stopping norms and as the restart rho of the FP32 PCG) and in FP64 across
+// blocks, in a fixed order.
 template <typename TZ>
 __global__ void __launch_bounds__(256)
 k_residual(const double *__restrict__ phi, const double *__restrict__ f,
@@ -506,34 +511,70 @@ k_residual(const double *__restrict__ phi, const double *__restrict__ f,
            const double *__restrict__ Wz, const double *__restrict__ diag, GridGeo g, PadGeo pg,
            TZ *__restrict__ zout, CgState *st, double *partials) {
     __shared__ double sred[8];
-    long long a = blockIdx.x * 256ll + threadIdx.x;
-    double rr = 0.0, rz = 0.0;
-    if (a < g.N) {
-        long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
-        bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
-        long long pa = (k * g.ny + j) * pg.sx + i;
-        if (interior) {
-            long long sy = g.nx, sz = (long long)g.nx * g.ny;
-            double x0 = phi[a];
-            double s = diag[a] * x0;
-            if (i > 1) s -= Wx[a - 1] * phi[a - 1];
-            if (i < g.nx - 2) s -= Wx[a] * phi[a + 1];
-            if (j > 1) s -= Wy[a - sy] * phi[a - sy];
-            if (j < g.ny - 2) s -= Wy[a] * phi[a + sy];
-            if (k > 1) s -= Wz[a - sz] * phi[a - sz];
-            if (k < g.nz - 2) s -= Wz[a] * phi[a + sz];
-            double r = f[a] - s;
-            TZ z;
-            if (sizeof(TZ) == 4) z = (TZ)((float)r / (float)diag[a]);
-            else z = (TZ)(r / diag[a]);
-            zout[pa] = z;
-            rr = r * r;
-            rz = r * (double)z;
+    __shared__ TZ sblk[2][8];
+    const long long stride = (long long)gridDim.x * 256;
+    const bool narrow = g.N <= 0x7fffffffll;
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    TZ rr = 0, rz = 0;
+    for (long long a = blockIdx.x * 256ll + threadIdx.x; a < g.N; a += stride) {
+        long long i, j, k;
+        if (narrow) {
+            unsigned ua = (unsigned)a, row = ua / (unsigned)g.nx;
+            i = ua - row * (unsigned)g.nx;
+            j = row % (unsigned)g.ny;
+            k = row / (unsigned)g.ny;
+        } else {
+            i = a % g.nx;
+            j = (a / g.nx) % g.ny;
+            k = a / sz;
         }
+        bool interior = i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+        if (!interior) continue;
+        double x0 = phi[a];
+        double sum = diag[a] * x0;
+        if (i > 1) sum -= Wx[a - 1] * phi[a - 1];
+        if (i < g.nx - 2) sum -= Wx[a] * phi[a + 1];
+        if (j > 1) sum -= Wy[a - sy] * phi[a - sy];
+        if (j < g.ny - 2) sum -= Wy[a] * phi[a + sy];
+        if (k > 1) sum -= Wz[a - sz] * phi[a - sz];
+        if (k < g.nz - 2) sum -= Wz[a] * phi[a + sz];
+        double r = f[a] - sum;
+        TZ z, rt;
+        if (sizeof(TZ) == 4) {
+            rt = (TZ)(float)r;
+            z = (TZ)((float)r / (float)diag[a]);
+        } else {
+            rt = (TZ)r;
+            z = (TZ)(r / diag[a]);
+        }
+        zout[(k * g.ny + j) * pg.sx + i] = z;
+        rr += rt * rt;
+        rz += rt * z;
+    }
+    // block sums in the accumulation type, then FP64 across blocks
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        rz += __shfl_down_sync(0xffffffffu, rz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sblk[0][threadIdx.x >> 5] = rr;
+        sblk[1][threadIdx.x >> 5] = rz;
+    }
+    __syncthreads();
+    double b0 = 0.0, b1 = 0.0;
+    if (threadIdx.x == 0) {
+        TZ t0 = 0, t1 = 0;
+        for (int q = 0; q < 8; ++q) {
+            t0 += sblk[0][q];
+            t1 += sblk[1][q];
+        }
+        b0 = (double)t0;
+        b1 = (double)t1;
     }
     int nb = gridDim.x;
     double t0, t1;
-    if (last_block_total<256, true>(st, partials, nb, rr, rz, sred, t0, t1)) {
+    if (last_block_total<256, true, true>(st, partials, nb, b0, b1, sred, t0, t1)) {
         if (threadIdx.x == 0) {
             st->res64 = t0;
             st->rz64 = t1;
@@ -874,9 +915,23 @@ pb_status sync_state(pb_system *sys, cudaStream_t s) {
     return PB_OK;
 }
 
+// resident blocks of a 256-thread kernel on the whole GPU
+template <class K>
+long long resident_blocks(K kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 2;
+    }
+    return (long long)per_sm * num_sms();
+}
+
 pb_status residual(pb_system *sys, bool fp32_out, cudaStream_t s) {
     const GridGeo &g = sys->g->geo;
-    unsigned blocks = cdiv(g.N, 256);
+    static const long long res32 = resident_blocks(k_residual<float>);
+    static const long long res64 = resident_blocks(k_residual<double>);
+    unsigned blocks = (unsigned)std::min<long long>(cdiv(g.N, 256), fp32_out ? res32 : res64);
     if (fp32_out)
         k_residual<float><<<blocks, 256, 0, s>>>(sys->phi, sys->rhs, sys->W[0], sys->W[1], sys->W[2],
                                                  sys->diag, g, sys->pad, sys->z32, sys->st,
