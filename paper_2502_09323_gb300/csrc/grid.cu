@@ -246,21 +246,33 @@ __global__ void k_cell_sort(const int *__restrict__ start, int *__restrict__ lis
 
 // ------------------------------------------------------- inside fraction --
 // Interval of the edge (x_a, x_a + h e_d) inside one ball, parameter t in
-// [0,1]: (u_d + t h)^2 = R^2 - |u_perp|^2 with u = x_a - c.
-__device__ __noinline__ bool ball_interval(const double xa[3], int d, double h, double cx,
-                                              double cy, double cz, double R, double &t0,
-                                              double &t1) {
-    double c[3] = {cx, cy, cz};
-    int e = (d == 0) ? 1 : 0;
-    int f = (d == 2) ? 1 : 2;
-    double ud = xa[d] - c[d];
-    double ue = xa[e] - c[e];
-    double uf = xa[f] - c[f];
+// [0,1]: (u_d + t h)^2 = R^2 - |u_perp|^2 with u = x_a - c.  Split in the part
+// that depends on the lattice line only (w = sqrt(R^2 - |u_perp|^2); false
+// when the line misses the ball) and the part for one edge of that line.
+__device__ __forceinline__ bool line_cut(const double xa[3], int d, double ce, double cf,
+                                         double R, double &w) {
+    const int e = (d == 0) ? 1 : 0;
+    const int f = (d == 2) ? 1 : 2;
+    double ue = xa[e] - ce;
+    double uf = xa[f] - cf;
     double s = R * R - (ue * ue + uf * uf);
     if (!(s > 0.0)) return false;
-    double w = sqrt(s);
-    double a0 = (-ud - w) / h;
-    double a1 = (-ud + w) / h;
+    w = sqrt(s);
+    return true;
+}
+
+// a0 = (-u_d - w)/h and a1 = (-u_d + w)/h clamped to [0,1]; false when the
+// clamped interval is empty.  The divisions are skipped where their sign or
+// their order against 1 already decides: a numerator >= h gives a0 >= 1 and a
+// numerator <= 0 gives a1 <= 0 (division by h > 0 is monotone), both empty.
+__device__ __forceinline__ bool edge_cut(double xad, double cd, double w, double h, double &t0,
+                                         double &t1) {
+    double ud = xad - cd;
+    double n0 = -ud - w;
+    double n1 = -ud + w;
+    if (n0 >= h || n1 <= 0.0) return false;
+    double a0 = n0 / h;
+    double a1 = n1 / h;
     if (a0 < 0.0) a0 = 0.0;
     if (a1 > 1.0) a1 = 1.0;
     if (!(a1 > a0)) return false;
@@ -271,6 +283,9 @@ __device__ __noinline__ bool ball_interval(const double xa[3], int d, double h, 
 
 // Measure of the union of the intervals of all balls meeting the edge; the
 // intervals are ordered by (t0, t1) and merged.  Returns false on overflow.
+// With COVER_EXIT the scan stops at the first ball whose interval is all of
+// [0, 1] (alpha = 1 exactly: the merged run then starts at 0 and ends at 1).
+template <bool COVER_EXIT>
 __device__ bool edge_alpha(const double *__restrict__ atoms, long long na, const CellList &cl,
                            const int *__restrict__ cstart, const int *__restrict__ clist,
                            const double xa[3], int d, double h, double &alpha) {
@@ -281,7 +296,10 @@ __device__ bool edge_alpha(const double *__restrict__ atoms, long long na, const
         double u = floor((xa[q] - cl.lo[q]) / cl.cs);
         cc[q] = (u < -4.0) ? -4 : ((u > (double)cl.dim[q] + 4.0) ? cl.dim[q] + 4 : (int)u);
     }
-    const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
+    const int e = (d == 0) ? 1 : 0;
+    const int f = (d == 2) ? 1 : 2;
+    const double *Ce = atoms + (long long)e * na, *Cf = atoms + (long long)f * na;
+    const double *Cd = atoms + (long long)d * na, *R = atoms + 3 * na;
     for (int cz = cc[2] - 1; cz <= cc[2] + 1; ++cz) {
         if (cz < 0 || cz >= cl.dim[2]) continue;
         for (int cy = cc[1] - 1; cy <= cc[1] + 1; ++cy) {
@@ -291,8 +309,13 @@ __device__ bool edge_alpha(const double *__restrict__ atoms, long long na, const
                 int cid = (cz * cl.dim[1] + cy) * cl.dim[0] + cx;
                 for (int s = cstart[cid]; s < cstart[cid + 1]; ++s) {
                     int at = clist[s];
-                    double t0, t1;
-                    if (!ball_interval(xa, d, h, X[at], Y[at], Z[at], R[at], t0, t1)) continue;
+                    double w, t0, t1;
+                    if (!line_cut(xa, d, Ce[at], Cf[at], R[at], w)) continue;
+                    if (!edge_cut(xa[d], Cd[at], w, h, t0, t1)) continue;
+                    if (COVER_EXIT && !(t0 > 0.0) && !(t1 < 1.0)) {
+                        alpha = 1.0;
+                        return true;
+                    }
                     if (m == MAX_EDGE_BALLS) return false;
                     // insertion by (t0, t1)
                     int b = m - 1;
@@ -351,7 +374,7 @@ __device__ __forceinline__ EdgeRef edge_ref(const GridGeo &g, long long e) {
 // 1 and the edge is listed exactly when its end nodes differ in `inside`.
 // One block per atom, one thread per lattice line (direction d and the node
 // indices of the two other axes) through the ball's bounding box.  Along a
-// line both a0 and a1 of ball_interval fall as the edge moves up (x_a[d]
+// line both a0 and a1 of edge_cut fall as the edge moves up (x_a[d]
 // enters through u_d = x_a[d] - c[d] and every rounded step after it is
 // monotone), so the scan going up stops at the first edge with t0 = 0 and the
 // scan coming down at the first with t1 = 1: every edge between the two has
@@ -363,8 +386,8 @@ __global__ void k_edge_cand(const double *__restrict__ atoms, long long na, Grid
     const int nn[3] = {g.nx, g.ny, g.nz};
     const long long step[3] = {1, (long long)g.nx, (long long)g.nx * g.ny};
     for (long long at = blockIdx.x; at < na; at += gridDim.x) {
-        const double cx = X[at], cy = Y[at], cz = Z[at], r = R[at];
-        const double c[3] = {cx, cy, cz};
+        const double c[3] = {X[at], Y[at], Z[at]};
+        const double r = R[at];
         long long lo[3], hi[3], ext[3];
         for (int d = 0; d < 3; ++d) {
             lo[d] = clampll((long long)floor((c[d] - r - g.o[d]) / g.h) - 1, 0, nn[d] - 1);
@@ -393,14 +416,16 @@ __global__ void k_edge_cand(const double *__restrict__ atoms, long long na, Grid
             const long long ihi = hi[d] < (long long)nn[d] - 2 ? hi[d] : (long long)nn[d] - 2;
             if (ihi < ilo) continue;
             double xa[3];
+            xa[d] = 0.0;
             xa[e] = node_coord(g, e, ie);
             xa[f] = node_coord(g, f, jf);
+            double w;
+            if (!line_cut(xa, d, c[e], c[f], r, w)) continue;
             const long long base = (long long)d * g.N + ie * step[e] + jf * step[f];
             long long iu = ihi + 1;
             for (long long i = ilo; i <= ihi; ++i) {
-                xa[d] = node_coord(g, d, i);
                 double t0, t1;
-                if (!ball_interval(xa, d, g.h, cx, cy, cz, r, t0, t1)) continue;
+                if (!edge_cut(node_coord(g, d, i), c[d], w, g.h, t0, t1)) continue;
                 if (t0 > 0.0 || t1 < 1.0) flags[base + i * step[d]] = 2;
                 if (!(t0 > 0.0)) {
                     iu = i;
@@ -408,9 +433,8 @@ __global__ void k_edge_cand(const double *__restrict__ atoms, long long na, Grid
                 }
             }
             for (long long i = ihi; i > iu; --i) {
-                xa[d] = node_coord(g, d, i);
                 double t0, t1;
-                if (!ball_interval(xa, d, g.h, cx, cy, cz, r, t0, t1)) continue;
+                if (!edge_cut(node_coord(g, d, i), c[d], w, g.h, t0, t1)) continue;
                 if (t0 > 0.0 || t1 < 1.0) flags[base + i * step[d]] = 2;
                 if (!(t1 < 1.0)) break;
             }
@@ -482,14 +506,17 @@ k_edge_flags(const double *__restrict__ atoms, long long na, GridGeo g, CellList
     for (int p = threadIdx.x; p < n; p += CHUNK_THREADS) {
         const int off = s_list[p];
         EdgeRef r = edge_ref(g, tile + off);
+        if (inside[r.a] != inside[r.b]) {
+            sb[off] = 1;
+            continue;
+        }
         double xa[3] = {node_coord(g, 0, r.ijk[0]), node_coord(g, 1, r.ijk[1]),
                         node_coord(g, 2, r.ijk[2])};
+        // an edge met by too many balls is listed, so that the record pass,
+        // which reports the overflow, meets it again
         double al;
-        if (!edge_alpha(atoms, na, cl, cstart, clist, xa, r.d, g.h, al)) {
-            atomicOr(&info->err, ERRF_TOO_MANY_BALLS);
-            al = 0.0;
-        }
-        sb[off] = ((al > 0.0 && al < 1.0) || inside[r.a] != inside[r.b]) ? 1 : 0;
+        if (!edge_alpha<true>(atoms, na, cl, cstart, clist, xa, r.d, g.h, al)) al = 0.5;
+        sb[off] = (al > 0.0 && al < 1.0) ? 1 : 0;
     }
     __syncthreads();
     reinterpret_cast<uint4 *>(flags)[(long long)blockIdx.x * CHUNK_THREADS + threadIdx.x] =
@@ -548,7 +575,10 @@ __global__ void k_cross_fill(const double *__restrict__ atoms, long long na, Gri
     double xa[3] = {node_coord(g, 0, r.ijk[0]), node_coord(g, 1, r.ijk[1]),
                     node_coord(g, 2, r.ijk[2])};
     double al;
-    if (!edge_alpha(atoms, na, cl, cstart, clist, xa, r.d, g.h, al)) al = 0.0;
+    if (!edge_alpha<false>(atoms, na, cl, cstart, clist, xa, r.d, g.h, al)) {
+        atomicOr(&info->err, ERRF_TOO_MANY_BALLS);
+        al = 0.0;
+    }
     alpha_out[s] = al;
     int ina = inside[r.a], inb = inside[r.b];
     double p[3] = {xa[0], xa[1], xa[2]};
@@ -719,10 +749,6 @@ pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
     PB_CUDA_TRY(cudaMemcpyAsync(&total, coffs + nchunks, sizeof(int), cudaMemcpyDeviceToHost, s));
     PB_CUDA_TRY(cudaMemcpyAsync(&hinfo, g->d_info, sizeof(BuildInfo), cudaMemcpyDeviceToHost, s));
     PB_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hinfo.err & ERRF_TOO_MANY_BALLS) {
-        set_error("more than %d atom balls meet one grid edge", MAX_EDGE_BALLS);
-        return PB_ERR_ARG;
-    }
     if (hinfo.err & ERRF_CELL_OVERFLOW) {
         set_error("internal: atom outside its cell list");
         return PB_ERR_CUDA;
@@ -752,6 +778,10 @@ pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
     dfree(coffs, s);
     PB_CUDA_TRY(cudaMemcpyAsync(&hinfo, g->d_info, sizeof(BuildInfo), cudaMemcpyDeviceToHost, s));
     PB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hinfo.err & ERRF_TOO_MANY_BALLS) {
+        set_error("more than %d atom balls meet one listed grid edge", MAX_EDGE_BALLS);
+        return PB_ERR_ARG;
+    }
     g->nflux = (long long)hinfo.nflux;
     g->ninside = (long long)hinfo.ninside;
     return PB_OK;

@@ -8,7 +8,8 @@
 // position is stored as an FP32 pair (hi + lo) relative to the grid centre so
 // the difference r_t - r_i keeps ~46 bits; 1/r from rsqrtf; each tile's
 // contributions are summed with Kahan compensation in FP32 and the tile sum
-// is added to an FP64 accumulator.
+// is added to an FP64 accumulator.  A thread's two targets share each
+// instruction through the packed FP32x2 arithmetic of sm_100-class GPUs.
 #include <cub/block/block_reduce.cuh>
 
 #include "pb_internal.h"
@@ -136,21 +137,31 @@ __device__ __forceinline__ TgtLoad load_target(const TargetDesc &T, long long t)
     return r;
 }
 
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-    float y = v - c;
-    float t = s + y;
-    c = (t - s) - y;
+// Packed FP32 pair: lane .x works for the thread's first target, .y for its
+// second (one FP32x2 instruction does both).
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
+}
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 v) {
+    float2 y = sub2(v, c);
+    float2 t = __fadd2_rn(s, y);
+    c = sub2(sub2(t, s), y);
     s = t;
 }
 
 // out_phi[t] = scale * sum_i q_i exp(-k r)/r; out_psi[t] = sum_i q_i (r.n)/r^3
-// (PSI only for surface targets).  Self pairs (r == 0) are skipped.
+// (PSI only for surface targets).  Self pairs (r == 0) are skipped.  Each
+// thread holds two targets in the two halves of FP32x2 registers; the
+// sources are staged in shared memory already duplicated into (v, v) pairs.
+static_assert(NB_TPT == 2, "two targets per thread, one per FP32x2 half");
 template <bool PSI, bool SCREEN>
 __global__ void __launch_bounds__(NB_THREADS)
 k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__ slo,
         long long ns, float kscr, double scale, double *__restrict__ out_phi,
         double *__restrict__ out_psi) {
-    __shared__ float4 sh[NB_THREADS], sl[NB_THREADS];
+    // per source: (hx,hx,hy,hy) (hz,hz,q,q) (lx,lx,ly,ly) (lz,lz,0,0)
+    __shared__ float4 sp4[NB_THREADS][4];
     long long t0 = ((long long)blockIdx.x * NB_THREADS * NB_TPT) + threadIdx.x;
     TgtLoad tg[NB_TPT];
     double acc_phi[NB_TPT], acc_psi[NB_TPT];
@@ -160,44 +171,57 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
         acc_phi[u] = 0.0;
         acc_psi[u] = 0.0;
     }
+    float2 th[3], tl[3], tn[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        th[d] = make_float2(tg[0].h[d], tg[1].h[d]);
+        tl[d] = make_float2(tg[0].l[d], tg[1].l[d]);
+        tn[d] = make_float2(tg[0].n[d], tg[1].n[d]);
+    }
     for (long long base = 0; base < ns; base += NB_THREADS) {
         long long si = base + threadIdx.x;
         __syncthreads();
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
         if (si < ns) {
-            sh[threadIdx.x] = shi[si];
-            sl[threadIdx.x] = slo[si];
-        } else {
-            sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-            sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a = shi[si];
+            b = slo[si];
         }
+        sp4[threadIdx.x][0] = make_float4(a.x, a.x, a.y, a.y);
+        sp4[threadIdx.x][1] = make_float4(a.z, a.z, a.w, a.w);
+        sp4[threadIdx.x][2] = make_float4(b.x, b.x, b.y, b.y);
+        sp4[threadIdx.x][3] = make_float4(b.z, b.z, 0.f, 0.f);
         __syncthreads();
         int m = (int)min((long long)NB_THREADS, ns - base);
-        float sp[NB_TPT], cp[NB_TPT], sq[NB_TPT], cq[NB_TPT];
-#pragma unroll
-        for (int u = 0; u < NB_TPT; ++u) sp[u] = cp[u] = sq[u] = cq[u] = 0.f;
+        float2 sp = bc2(0.f), cp = bc2(0.f), sq = bc2(0.f), cq = bc2(0.f);
 #pragma unroll 4
         for (int q = 0; q < m; ++q) {
-            float4 a = sh[q], b = sl[q];
-#pragma unroll
-            for (int u = 0; u < NB_TPT; ++u) {
-                float dx = (tg[u].h[0] - a.x) + (tg[u].l[0] - b.x);
-                float dy = (tg[u].h[1] - a.y) + (tg[u].l[1] - b.y);
-                float dz = (tg[u].h[2] - a.z) + (tg[u].l[2] - b.z);
-                float r2 = dx * dx + dy * dy + dz * dz;
-                float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                float v = a.w * ri;
-                if (SCREEN) v *= expf(-kscr * (r2 * ri));
-                kahan_add(sp[u], cp[u], v);
-                if (PSI) {
-                    float dn = dx * tg[u].n[0] + dy * tg[u].n[1] + dz * tg[u].n[2];
-                    kahan_add(sq[u], cq[u], v * dn * (ri * ri));
-                }
+            const float4 p0 = sp4[q][0], p1 = sp4[q][1], p2 = sp4[q][2], p3 = sp4[q][3];
+            const float2 dx = __fadd2_rn(sub2(th[0], make_float2(p0.x, p0.y)),
+                                         sub2(tl[0], make_float2(p2.x, p2.y)));
+            const float2 dy = __fadd2_rn(sub2(th[1], make_float2(p0.z, p0.w)),
+                                         sub2(tl[1], make_float2(p2.z, p2.w)));
+            const float2 dz = __fadd2_rn(sub2(th[2], make_float2(p1.x, p1.y)),
+                                         sub2(tl[2], make_float2(p3.x, p3.y)));
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f,
+                                          r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+            float2 v = __fmul2_rn(make_float2(p1.z, p1.w), ri);
+            if (SCREEN) {
+                v.x *= expf(-kscr * (r2.x * ri.x));
+                v.y *= expf(-kscr * (r2.y * ri.y));
+            }
+            kahan_add2(sp, cp, v);
+            if (PSI) {
+                const float2 dn =
+                    __ffma2_rn(dz, tn[2], __ffma2_rn(dy, tn[1], __fmul2_rn(dx, tn[0])));
+                kahan_add2(sq, cq, __fmul2_rn(__fmul2_rn(v, dn), __fmul2_rn(ri, ri)));
             }
         }
-#pragma unroll
-        for (int u = 0; u < NB_TPT; ++u) {
-            acc_phi[u] += (double)sp[u] - (double)cp[u];
-            if (PSI) acc_psi[u] += (double)sq[u] - (double)cq[u];
+        acc_phi[0] += (double)sp.x - (double)cp.x;
+        acc_phi[1] += (double)sp.y - (double)cp.y;
+        if (PSI) {
+            acc_psi[0] += (double)sq.x - (double)cq.x;
+            acc_psi[1] += (double)sq.y - (double)cq.y;
         }
     }
 #pragma unroll

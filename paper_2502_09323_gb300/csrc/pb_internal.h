@@ -37,7 +37,7 @@ void dfree(void *p, cudaStream_t s);
 enum : uint32_t {
     ERRF_ATOM_VALUE = 1u,      // NaN/Inf coordinate or non-positive radius
     ERRF_CHARGE_CELL = 2u,     // a charge's trilinear cell touches the boundary
-    ERRF_TOO_MANY_BALLS = 4u,  // more than MAX_EDGE_BALLS balls meet one edge
+    ERRF_TOO_MANY_BALLS = 4u,  // more than MAX_EDGE_BALLS balls meet one listed edge
     ERRF_CELL_OVERFLOW = 8u,   // atom cell list inconsistent
 };
 constexpr int MAX_EDGE_BALLS = 48;

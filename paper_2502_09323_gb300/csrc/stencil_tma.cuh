@@ -528,36 +528,58 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                         }
                     }
                 } else {
+                    // per-point weights, packed like the fast path: points
+                    // (0,1) and (2,3) of this lane, each FP32x2 step rounding
+                    // as the scalar expression it stands for
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int i = ib + q;
-                        const uint8_t c0 = (uint8_t)(cc >> (8 * q));
-                        const float x0 = pc[q];
-                        const float xl = q > 0 ? pc[q - 1] : left;
-                        const float xr = q < 3 ? pc[q + 1] : right;
-                        const float kp = cp.kappa(c0);
-                        float ap = kp * x0;
-                        ap += wxm[q] * (x0 - xl);
-                        ap += wxp[q] * (x0 - xr);
-                        ap += wym[q] * (x0 - ym[q]);
-                        ap += wyp[q] * (x0 - yp[q]);
-                        ap += wzm[q] * (x0 - pm[q]);
-                        ap += wzp[q] * (x0 - pn[q]);
-                        const float dg = ((((((wxm[q] + wxp[q]) + wym[q]) + wyp[q]) + wzm[q]) + wzp[q]) + kp);
-                        const float dinv = 1.f / dg;
-                        const bool interior = grp_ok && i >= 1 && i <= g.nx - 2;
-                        y[q] = interior ? ap : 0.f;
+                    for (int h = 0; h < 2; ++h) {
+                        const int q0 = 2 * h;
+                        const uint8_t ca = (uint8_t)(cc >> (8 * q0)), cb = (uint8_t)(cc >> (8 * q0 + 8));
+                        const float2 x = f2(pc[q0], pc[q0 + 1]);
+                        const float2 xl = f2(q0 == 0 ? left : pc[q0 - 1], pc[q0]);
+                        const float2 xr = f2(pc[q0 + 1], q0 == 2 ? right : pc[q0 + 2]);
+                        const float2 kp = f2(cp.kappa(ca), cp.kappa(cb));
+                        const float2 w0 = f2(wxm[q0], wxm[q0 + 1]), w1 = f2(wxp[q0], wxp[q0 + 1]);
+                        const float2 w2 = f2(wym[q0], wym[q0 + 1]), w3 = f2(wyp[q0], wyp[q0 + 1]);
+                        const float2 w4 = f2(wzm[q0], wzm[q0 + 1]), w5 = f2(wzp[q0], wzp[q0 + 1]);
+                        float2 ap = __fmul2_rn(kp, x);
+                        ap = __ffma2_rn(w0, sub2(x, xl), ap);
+                        ap = __ffma2_rn(w1, sub2(x, xr), ap);
+                        ap = __ffma2_rn(w2, sub2(x, f2(ym[q0], ym[q0 + 1])), ap);
+                        ap = __ffma2_rn(w3, sub2(x, f2(yp[q0], yp[q0 + 1])), ap);
+                        ap = __ffma2_rn(w4, sub2(x, f2(pm[q0], pm[q0 + 1])), ap);
+                        ap = __ffma2_rn(w5, sub2(x, f2(pn[q0], pn[q0 + 1])), ap);
+                        const bool ia = grp_ok && ib + q0 >= 1 && ib + q0 <= g.nx - 2;
+                        const bool ib2 = grp_ok && ib + q0 + 1 >= 1 && ib + q0 + 1 <= g.nx - 2;
                         if (MODE == MODE_P) {
-                            if (interior) acc0 += x0 * ap;
+                            const float2 c = __fmul2_rn(x, ap);
+                            if (ia) acc0 += c.x;
+                            if (ib2) acc0 += c.y;
                         } else if (MODE == MODE_U) {
-                            if (interior) {
-                                xv[q] = xv[q] + alpha * x0;
-                                const float znew = zv[q] - alpha * ap * dinv;
-                                zv[q] = znew;
-                                const float rr = dg * znew;
-                                acc0 += rr * znew;
-                                acc1 += rr * rr;
+                            const float2 dg = __fadd2_rn(
+                                __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(w0, w1), w2), w3), w4), w5),
+                                kp);
+                            const float2 ndinv = f2(-1.f / dg.x, -1.f / dg.y);
+                            const float2 xn = __ffma2_rn(f2(alpha, alpha), x, f2(xv[q0], xv[q0 + 1]));
+                            const float2 zn = __ffma2_rn(__fmul2_rn(f2(alpha, alpha), ap), ndinv,
+                                                         f2(zv[q0], zv[q0 + 1]));
+                            const float2 rr = __fmul2_rn(dg, zn);
+                            const float2 c0 = __fmul2_rn(rr, zn), c1 = __fmul2_rn(rr, rr);
+                            if (ia) {
+                                xv[q0] = xn.x;
+                                zv[q0] = zn.x;
+                                acc0 += c0.x;
+                                acc1 += c1.x;
                             }
+                            if (ib2) {
+                                xv[q0 + 1] = xn.y;
+                                zv[q0 + 1] = zn.y;
+                                acc0 += c0.y;
+                                acc1 += c1.y;
+                            }
+                        } else {
+                            y[q0] = ia ? ap.x : 0.f;
+                            y[q0 + 1] = ib2 ? ap.y : 0.f;
                         }
                     }
                 }

@@ -257,3 +257,17 @@ def test_argument_errors(pb):
     rc = pb._native.lib().pb_build_grid(ctypes.byref(spec), good.ctypes.data_as(ctypes.c_void_p),
                                         len(good), 0, None, ctypes.byref(h))
     assert rc == -1
+
+
+def test_too_many_balls_on_one_edge(pb):
+    """Sixty coincident uncharged balls cut the same listed edges: more than
+    the 48 intervals one edge holds, reported as an argument error.  One ball
+    fewer than the limit builds."""
+    from paper_2502_09323_gb300 import PBError
+    spec = pb.GridSpec(n=(33, 33, 33), origin=(-8.0, -8.0, -8.0), h=0.5)
+    ball = [0.1, 0.2, 0.3, 1.3, 0.0]
+    with pytest.raises(PBError, match="balls meet one listed grid edge"):
+        pb.pb_build_grid(spec, np.array([ball] * 60))
+    g = pb.pb_build_grid(spec, np.array([ball] * 48))
+    assert g.info.n_cross > 0
+    g.free()
