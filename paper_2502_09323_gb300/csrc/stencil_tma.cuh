@@ -559,7 +559,8 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                             const float2 dg = __fadd2_rn(
                                 __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(w0, w1), w2), w3), w4), w5),
                                 kp);
-                            const float2 ndinv = f2(-1.f / dg.x, -1.f / dg.y);
+                            // hardware reciprocal (about 1 ulp): a Jacobi scale inside the FP32 solve
+                            const float2 ndinv = f2(-__fdividef(1.f, dg.x), -__fdividef(1.f, dg.y));
                             const float2 xn = __ffma2_rn(f2(alpha, alpha), x, f2(xv[q0], xv[q0 + 1]));
                             const float2 zn = __ffma2_rn(__fmul2_rn(f2(alpha, alpha), ap), ndinv,
                                                          f2(zv[q0], zv[q0 + 1]));
