@@ -751,12 +751,28 @@ dim3 tma_grid(const PadGeo &g, int) {
 
 template <int MODE>
 void tma_launch(const tma::SysEntry *dev_tab, int nsys, int total_items, unsigned int *queue,
-                dim3 grid, cudaStream_t s, const tma::SysEntry *host_e0 = nullptr) {
+                dim3 grid, cudaStream_t s, const tma::SysEntry *host_e0 = nullptr,
+                bool overlap = false) {
     // host_e0: the host copy of the entry of a one-system launch, passed by
     // value (the single-system kernel reads everything of it from the
-    // parameter bank); nullptr or several systems: the table form
+    // parameter bank); nullptr or several systems: the table form.
+    // overlap: programmatic stream serialization, so that this launch's
+    // blocks start (and set up) while the previous stencil kernel drains.
     static const tma::SysEntry zero{};
-    if (host_e0 && nsys == 1)
+    if (host_e0 && nsys == 1 && overlap) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(tma::NTHREADS);
+        cfg.dynamicSmemBytes = tma::smem_bytes<MODE>();
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_stencil_tma<MODE, true>, dev_tab, nsys, total_items, queue,
+                           *host_e0);
+    } else if (host_e0 && nsys == 1)
         k_stencil_tma<MODE, true><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(
             dev_tab, nsys, total_items, queue, *host_e0);
     else
@@ -853,8 +869,8 @@ void launch_iter_tma(pb_system *sys, const CoefC32 &, int cur, int KC, cudaStrea
     TmaState *t = (TmaState *)sys->tma;
     if (tma_use_kc(sys, KC, s) != PB_OK) return;
     dim3 grid = tma_grid(sys->pad, KC);
-    tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
-    tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
+    tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
+    tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
 }
 
 CoefC32 make_c32(const pb_system *sys) {
@@ -1388,11 +1404,11 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
             if ((rc = tma_use_kc(sys, KC, s)) != PB_OK) return rc;
             dim3 grid = tma_grid(sys->pad, KC);
             if (which == 0 || which == 2) {
-                tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
+                tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
                 PB_LAUNCH_CHECK();
             }
             if (which == 1 || which == 2) {
-                tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host);
+                tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
                 PB_LAUNCH_CHECK();
             }
         } else if (precision == PB_MIXED) {

@@ -193,6 +193,16 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
         for (int q = 0; q < NSLOT; ++q) s_pcnt[q] = 0u;
+    }
+    // Programmatic dependent launch.  The set-up above touches only this
+    // block's shared memory; the work counters, the CG state and the vectors
+    // below are written by the previous kernel of the stream, so every thread
+    // waits here for that kernel to complete (a no-op unless the launch asked
+    // for programmatic serialization).  The next kernel may then be scheduled
+    // as SMs free up; it waits the same way before touching our results.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (threadIdx.x == 0) {
         s_nsys = nsys < 0 ? (int)((volatile unsigned int *)queue)[2] : nsys;
         s_total = nsys < 0 ? (int)((volatile unsigned int *)queue)[3] : total_items;
     }
