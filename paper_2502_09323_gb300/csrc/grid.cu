@@ -378,10 +378,12 @@ __device__ __forceinline__ EdgeRef edge_ref(const GridGeo &g, long long e) {
 // enters through u_d = x_a[d] - c[d] and every rounded step after it is
 // monotone), so the scan going up stops at the first edge with t0 = 0 and the
 // scan coming down at the first with t1 = 1: every edge between the two has
-// the interval [0, 1].  Candidates get flag byte 2 (several balls may write
-// the same byte, with the same value).
+// the interval [0, 1].  Candidates get flag byte 2, and the edges whose
+// interval for this ball is all of [0, 1] get cov byte 1: on those the union
+// is [0, 1] whatever the other balls add, so alpha = 1 exactly.  (Several
+// balls may write the same byte, always with the same value.)
 __global__ void k_edge_cand(const double *__restrict__ atoms, long long na, GridGeo g,
-                            uint8_t *__restrict__ flags) {
+                            uint8_t *__restrict__ flags, uint8_t *__restrict__ cov) {
     const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
     const int nn[3] = {g.nx, g.ny, g.nz};
     const long long step[3] = {1, (long long)g.nx, (long long)g.nx * g.ny};
@@ -422,13 +424,15 @@ __global__ void k_edge_cand(const double *__restrict__ atoms, long long na, Grid
             double w;
             if (!line_cut(xa, d, c[e], c[f], r, w)) continue;
             const long long base = (long long)d * g.N + ie * step[e] + jf * step[f];
-            long long iu = ihi + 1;
+            long long iu = ihi + 1, id = ihi + 1;
+            bool cov_iu = false;
             for (long long i = ilo; i <= ihi; ++i) {
                 double t0, t1;
                 if (!edge_cut(node_coord(g, d, i), c[d], w, g.h, t0, t1)) continue;
                 if (t0 > 0.0 || t1 < 1.0) flags[base + i * step[d]] = 2;
                 if (!(t0 > 0.0)) {
                     iu = i;
+                    cov_iu = !(t1 < 1.0);
                     break;
                 }
             }
@@ -436,29 +440,44 @@ __global__ void k_edge_cand(const double *__restrict__ atoms, long long na, Grid
                 double t0, t1;
                 if (!edge_cut(node_coord(g, d, i), c[d], w, g.h, t0, t1)) continue;
                 if (t0 > 0.0 || t1 < 1.0) flags[base + i * step[d]] = 2;
-                if (!(t1 < 1.0)) break;
+                if (!(t1 < 1.0)) {
+                    id = i;
+                    break;
+                }
             }
+            // covered: iu when its t1 is 1, and every edge from iu + 1 to id
+            if (cov_iu) cov[base + iu * step[d]] = 1;
+            if (id <= ihi)
+                for (long long i = iu + 1; i <= id; ++i) cov[base + i * step[d]] = 1;
         }
     }
 }
 
 // flag[e] = 1 when edge e is listed: 0 < alpha < 1 or its end nodes differ in
-// `inside`.  One block per 4096 edges: non-candidate bytes get the inside
-// test, the tile's candidates are gathered in shared memory and shared out
-// over the block for the full inside fraction (union of all balls' intervals).
+// `inside`.  One block per 4096 edges.  Edges whose end nodes differ are
+// listed; the others are listed only if they are candidates not covered by
+// one ball, and for those the block computes the inside fraction (union of
+// all balls' intervals): they are gathered in shared memory and shared out
+// over the block.
 __global__ void __launch_bounds__(CHUNK_THREADS)
 k_edge_flags(const double *__restrict__ atoms, long long na, GridGeo g, CellList cl,
              const int *__restrict__ cstart, const int *__restrict__ clist,
-             const uint8_t *__restrict__ inside, uint8_t *__restrict__ flags, BuildInfo *info) {
+             const uint8_t *__restrict__ inside, uint8_t *__restrict__ flags,
+             const uint8_t *__restrict__ cov, BuildInfo *info) {
     __shared__ uint4 s_fl[CHUNK_THREADS];
     __shared__ int s_list[CHUNK_BYTES];
-    __shared__ int s_n;
-    if (threadIdx.x == 0) s_n = 0;
+    __shared__ int s_list_n;
+    if (threadIdx.x == 0) s_list_n = 0;
     __syncthreads();
     const long long tile = (long long)blockIdx.x * CHUNK_BYTES;
     uint4 v = reinterpret_cast<const uint4 *>(flags)[(long long)blockIdx.x * CHUNK_THREADS +
                                                      threadIdx.x];
     unsigned w[4] = {v.x, v.y, v.z, v.w};
+    uint4 cv = make_uint4(0u, 0u, 0u, 0u);
+    if (v.x | v.y | v.z | v.w)
+        cv = reinterpret_cast<const uint4 *>(cov)[(long long)blockIdx.x * CHUNK_THREADS +
+                                                 threadIdx.x];
+    const unsigned cw[4] = {cv.x, cv.y, cv.z, cv.w};
     // first edge of this thread's 16, then stepped node by node
     long long e0 = tile + 16ll * threadIdx.x;
     int d = (int)(e0 / g.N);
@@ -473,14 +492,16 @@ k_edge_flags(const double *__restrict__ atoms, long long na, GridGeo g, CellList
             unsigned u = (w[q] >> (8 * b)) & 0xffu;
             unsigned fl = 0;
             if (d < 3) {
-                if (u == 2u) {
-                    int p = atomicAdd(&s_n, 1);
+                long long id = d == 0 ? i : (d == 1 ? j : k);
+                long long nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+                long long st = d == 0 ? 1 : (d == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+                const bool differ = id < nd - 1 && inside[a] != inside[a + st];
+                const bool covered = ((cw[q] >> (8 * b)) & 0xffu) != 0u;
+                if (u == 2u && !differ && !covered) {
+                    int p = atomicAdd(&s_list_n, 1);
                     s_list[p] = 16 * threadIdx.x + 4 * q + b;
-                } else {
-                    long long id = d == 0 ? i : (d == 1 ? j : k);
-                    long long nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
-                    long long st = d == 0 ? 1 : (d == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
-                    if (id < nd - 1 && inside[a] != inside[a + st]) fl = 1;
+                } else if (differ) {
+                    fl = 1;
                 }
             }
             out |= fl << (8 * b);
@@ -502,14 +523,10 @@ k_edge_flags(const double *__restrict__ atoms, long long na, GridGeo g, CellList
     s_fl[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
     __syncthreads();
     uint8_t *sb = reinterpret_cast<uint8_t *>(s_fl);
-    const int n = s_n;
+    const int n = s_list_n;
     for (int p = threadIdx.x; p < n; p += CHUNK_THREADS) {
         const int off = s_list[p];
         EdgeRef r = edge_ref(g, tile + off);
-        if (inside[r.a] != inside[r.b]) {
-            sb[off] = 1;
-            continue;
-        }
         double xa[3] = {node_coord(g, 0, r.ijk[0]), node_coord(g, 1, r.ijk[1]),
                         node_coord(g, 2, r.ijk[2])};
         // an edge met by too many balls is listed, so that the record pass,
@@ -729,18 +746,21 @@ pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
     long long nchunks = (nedge + CHUNK_BYTES - 1) / CHUNK_BYTES;
     long long nflags = nchunks * CHUNK_BYTES;
     uint8_t *flags = (uint8_t *)dalloc(nflags, s);
+    uint8_t *cov = (uint8_t *)dalloc(nflags, s);
     int *ccount = (int *)dalloc(sizeof(int) * (nchunks + 1), s);
     int *coffs = (int *)dalloc(sizeof(int) * (nchunks + 1), s);
-    if (!flags || !ccount || !coffs) return PB_ERR_OOM;
+    if (!flags || !cov || !ccount || !coffs) return PB_ERR_OOM;
     PB_CUDA_TRY(cudaMemsetAsync(flags, 0, nflags, s));
+    PB_CUDA_TRY(cudaMemsetAsync(cov, 0, nflags, s));
     if (na > 0) {
-        k_edge_cand<<<atom_blocks, 128, 0, s>>>(g->atoms, na, geo, flags);
+        k_edge_cand<<<atom_blocks, 128, 0, s>>>(g->atoms, na, geo, flags, cov);
         PB_LAUNCH_CHECK();
     }
     k_edge_flags<<<(unsigned)nchunks, CHUNK_THREADS, 0, s>>>(g->atoms, na, geo, cl, cl.start,
-                                                              cl.atom, g->inside, flags,
+                                                              cl.atom, g->inside, flags, cov,
                                                               g->d_info);
     PB_LAUNCH_CHECK();
+    dfree(cov, s);
     k_chunk_count<<<(unsigned)nchunks, CHUNK_THREADS, 0, s>>>((const uint4 *)flags, ccount);
     PB_LAUNCH_CHECK();
     k_scan_int<1024><<<1, 1024, 0, s>>>(ccount, coffs, (int)nchunks);

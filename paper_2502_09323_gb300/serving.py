@@ -83,8 +83,10 @@ def _octree_estimate(spec: OctreeSpec, atoms: np.ndarray) -> int:
         h *= 2.0
     slots += (side / spec.h_bulk) ** 3
     edges = OCT_EDGES_PER_ATOM * len(atoms) * (0.25 / spec.h_fine) ** 2
-    # the build classifies the whole domain on the finest lattice (freed after)
-    transient = 6.0 * (side / spec.h_fine + 1) ** 3
+    # the build classifies the whole domain on the finest lattice (freed
+    # after): an inside byte per node, listed-edge and covered-edge bytes per
+    # edge, and a byte per node of margin
+    transient = 8.0 * (side / spec.h_fine + 1) ** 3
     return int(OCT_BYTES_PER_SLOT * slots + OCT_BYTES_PER_EDGE * edges + transient) + FIXED_BYTES
 
 
