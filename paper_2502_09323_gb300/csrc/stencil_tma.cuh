@@ -142,6 +142,10 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap *map, 
 
 // packed FP32 pairs (two independent lanes of arithmetic per instruction)
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+// hint: bring the line holding p into L1 (no register result, no wait)
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.L1 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
@@ -370,6 +374,29 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             zg = e0.z;
             ksys = 0;
         }
+        // Listed weights of this row at plane kp (codes in slot sl) go to L1
+        // one plane before the slow path reads them, so that its gathers hit
+        // L1 instead of waiting on DRAM (update kernel only: measured, it
+        // shortens the update kernel and lengthens the direction kernel).  The addresses are exactly those the
+        // slow path loads (own +x/+y/+z, the -y face from the row below, lane
+        // 0's -x face, and the -z face from czb, the plane below's codes, when
+        // its weights are not carried over from the previous plane); the
+        // four points of a lane and face share one 16-byte run.
+        auto prefetch_w = [&](const uint8_t *sl, int kp, int j, int ib, uint32_t cown,
+                              uint32_t czb) {
+            const uint32_t cyb = code4(sl, r - 1);
+            const uint32_t lc = lane == 0 ? (uint32_t)sl[L::code + r * CODEW + 15] : 0u;
+            const uint32_t need = (cown & 0x0E0E0E0Eu) | (cyb & 0x04040404u) |
+                                  (czb & 0x08080808u) | (lc & 2u);
+            if (!__any_sync(0xffffffffu, need != 0u)) return;
+            const int pl = kp * (int)g.sxy + j * g.sx + ib;
+            if (cown & 0x02020202u) prefetch_l1(cp.wx + pl);
+            if (cown & 0x04040404u) prefetch_l1(cp.wy + pl);
+            if (cown & 0x08080808u) prefetch_l1(cp.wz + pl);
+            if (cyb & 0x04040404u) prefetch_l1(cp.wy + pl - g.sx);
+            if (czb & 0x08080808u) prefetch_l1(cp.wz + pl - (int)g.sxy);
+            if (lc & 2u) prefetch_l1(cp.wx + pl - 1);
+        };
         for (;; ++nseg) {
             // the chunk's first plane's barrier also publishes its descriptor
             if (!wait_full(gt)) break;
@@ -419,6 +446,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 const uint8_t *s1 = slot_ptr(gt0 + 1);
                 val4(s1, r, pc);
                 cc = code4(s1, r);
+                if (MODE == MODE_U) prefetch_w(s1, kfirst, j, ib, cc, cm);
             }
             for (int t = 1; ok && t <= len; ++t) {
                 const int k = kfirst + t - 1;
@@ -429,6 +457,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 const uint8_t *sc = slot_ptr(gt0 + t), *sn = slot_ptr(gt0 + t + 1);
                 val4(sn, r, pn);
                 cn = code4(sn, r);
+                if (MODE == MODE_U && t < len) prefetch_w(sn, k + 1, j, ib, cn, 0u);
                 float ym[4], yp[4];
                 val4(sc, r - 1, ym);
                 val4(sc, r + 1, yp);
