@@ -142,8 +142,10 @@ k_prep(const double *__restrict__ atoms, long long na, int auto_place, int nmax,
 
 // --------------------------------------------------------- classification --
 // Node a is inside when (dx*dx + dy*dy) + dz*dz < R*R for some atom.  One
-// block per atom over the nodes of the ball's bounding box (one node of
-// margin on each side).
+// block per atom over the z-columns of the ball's bounding box (one node of
+// margin on each side): a column keeps its dx*dx + dy*dy, and one whose
+// value already reaches R*R holds no inside node (adding dz*dz >= 0 cannot
+// lower it).
 __global__ void k_classify(const double *__restrict__ atoms, long long na, GridGeo g,
                            uint8_t *__restrict__ inside) {
     const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
@@ -157,17 +159,19 @@ __global__ void k_classify(const double *__restrict__ atoms, long long na, GridG
             hi[d] = clampll((long long)ceil((c[d] + r - g.o[d]) / g.h) + 1, 0, nn[d] - 1);
             ext[d] = hi[d] - lo[d] + 1;
         }
-        double R2 = r * r;
-        long long tot = ext[0] * ext[1] * ext[2];
-        for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
-            long long i = lo[0] + t % ext[0];
-            long long j = lo[1] + (t / ext[0]) % ext[1];
-            long long k = lo[2] + t / (ext[0] * ext[1]);
-            double dx = node_coord(g, 0, i) - c[0];
-            double dy = node_coord(g, 1, j) - c[1];
-            double dz = node_coord(g, 2, k) - c[2];
-            double d2 = (dx * dx + dy * dy) + dz * dz;
-            if (d2 < R2) inside[(k * g.ny + j) * g.nx + i] = 1;
+        const double R2 = r * r;
+        const long long cols = ext[0] * ext[1];
+        for (long long t = threadIdx.x; t < cols; t += blockDim.x) {
+            const long long i = lo[0] + t % ext[0];
+            const long long j = lo[1] + t / ext[0];
+            const double dx = node_coord(g, 0, i) - c[0];
+            const double dy = node_coord(g, 1, j) - c[1];
+            const double q = dx * dx + dy * dy;
+            if (!(q < R2)) continue;
+            for (long long k = lo[2]; k <= hi[2]; ++k) {
+                const double dz = node_coord(g, 2, k) - c[2];
+                if (q + dz * dz < R2) inside[(k * g.ny + j) * g.nx + i] = 1;
+            }
         }
     }
 }
@@ -262,19 +266,19 @@ __device__ __forceinline__ bool line_cut(const double xa[3], int d, double ce, d
 }
 
 // a0 = (-u_d - w)/h and a1 = (-u_d + w)/h clamped to [0,1]; false when the
-// clamped interval is empty.  The divisions are skipped where their sign or
-// their order against 1 already decides: a numerator >= h gives a0 >= 1 and a
-// numerator <= 0 gives a1 <= 0 (division by h > 0 is monotone), both empty.
+// clamped interval is empty.  A division is skipped where the numerator
+// already decides its clamped value (division by h > 0 is monotone and
+// exact at h): n0 >= h gives a0 >= 1 and n1 <= 0 gives a1 <= 0 (empty),
+// n0 <= 0 gives t0 = 0 and n1 >= h gives t1 = 1.  (A clamped -0 becomes +0,
+// which changes no comparison and no union length.)
 __device__ __forceinline__ bool edge_cut(double xad, double cd, double w, double h, double &t0,
                                          double &t1) {
     double ud = xad - cd;
     double n0 = -ud - w;
     double n1 = -ud + w;
     if (n0 >= h || n1 <= 0.0) return false;
-    double a0 = n0 / h;
-    double a1 = n1 / h;
-    if (a0 < 0.0) a0 = 0.0;
-    if (a1 > 1.0) a1 = 1.0;
+    double a0 = n0 > 0.0 ? n0 / h : 0.0;
+    double a1 = n1 < h ? n1 / h : 1.0;
     if (!(a1 > a0)) return false;
     t0 = a0;
     t1 = a1;
