@@ -783,7 +783,7 @@ void tma_launch(const tma::SysEntry *dev_tab, int nsys, int total_items, unsigne
 struct TmaState {
     tma::SysEntry host;          // this system's launch-table entry
     tma::SysEntry *dev = nullptr;  // device copy (a table of one)
-    double *partials = nullptr;  // per (item, warp) dot-product slots
+    float *partials = nullptr;   // per-item dot-product slots
     unsigned int *cnt = nullptr;
     int uploaded_kc = -1;
     int max_items = 0;
@@ -831,7 +831,7 @@ pb_status build_tma_state(pb_system *sys) {
     t->max_items = tma_items(sys->pad, 4);
     if (rc == PB_OK) {
         t->dev = (tma::SysEntry *)dalloc(sizeof(tma::SysEntry), s);
-        t->partials = (double *)dalloc(sizeof(double) * 3 * (size_t)t->max_items * tma::ROWS, s);
+        t->partials = (float *)dalloc(sizeof(float) * 3 * (size_t)t->max_items, s);
         t->cnt = (unsigned int *)dalloc(4 * sizeof(unsigned int), s);
         if (!t->dev || !t->partials || !t->cnt) rc = PB_ERR_OOM;
     }

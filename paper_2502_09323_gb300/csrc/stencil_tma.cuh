@@ -95,8 +95,8 @@ struct SysEntry {  // aligned as CUtensorMap
     float *x, *z;       // solution increment, preconditioned residual
     float *y;           // apply output
     CgState *st;
-    double *partials;   // per (item, warp) slot q = li*ROWS + w: sigma at [q],
-                        // rho and rr at [nitems*ROWS + 2q], [.. + 1]
+    float *partials;    // per item li: sigma at [li], rho and rr at
+                        // [nitems + 2 li] and [nitems + 2 li + 1]
     unsigned int *cnt;  // items finished in the current launch
     int xtiles, ytiles, nchunk, KC, nitems, item_base;
 };
@@ -155,10 +155,21 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// compensated FP32 sum (Neumaier): the value is s + c
+__device__ __forceinline__ void nsum(float &s, float &c, float v) {
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+// the warp's compensated sums combined in a fixed tree (lane 0 holds them)
+__device__ __forceinline__ void warp_nsum(float &s, float &c) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+        nsum(s, c, s2);
+        c += c2;
+    }
 }
 
 }  // namespace tma
@@ -183,7 +194,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
     __shared__ int s_desc[NSLOT][7];  // i0, j0, kfirst, len, system, local item, parity
     // per-descriptor warp partials of the dot products, combined without a
     // barrier: the warp that completes a descriptor's count sums them
-    __shared__ double s_part[NSLOT][ROWS][2];
+    __shared__ float s_part[NSLOT][ROWS][2];
     __shared__ unsigned s_pcnt[NSLOT];
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -659,15 +670,15 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             const float b0 = warp_sum_f(acc0), b1 = warp_sum_f(acc1);
             const int ps = nseg % NSLOT;
             if (lane == 0) {
-                s_part[ps][w][0] = (double)b0;
-                s_part[ps][w][1] = (double)b1;
+                s_part[ps][w][0] = b0;
+                s_part[ps][w][1] = b1;
                 __threadfence_block();
                 if (atomicAdd(&s_pcnt[ps], 1u) == (unsigned)ROWS - 1) {
                     __threadfence_block();
-                    double t0 = 0.0, t1 = 0.0;
+                    float t0 = 0.f, t1 = 0.f;
                     for (int r = 0; r < ROWS; ++r) {
-                        t0 += *(volatile double *)&s_part[ps][r][0];
-                        t1 += *(volatile double *)&s_part[ps][r][1];
+                        t0 += *(volatile float *)&s_part[ps][r][0];
+                        t1 += *(volatile float *)&s_part[ps][r][1];
                     }
                     s_pcnt[ps] = 0u;
                     const int nit = e->nitems;
@@ -705,8 +716,10 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
     if (MODE != MODE_A) {
         // Each system's item partials are summed in an order fixed by its
         // item count only: systems of more than BIGSYS items by the whole
-        // block (thread t takes items t, t+NTHREADS, ... into four
-        // accumulators), smaller ones by one warp each.
+        // block (thread t takes items t, t+NTHREADS, ...), smaller ones by
+        // one warp each.  The sums are compensated FP32 up to the warps'
+        // totals (this block runs alone at the end of the launch, on the
+        // critical path, and FP64 is a narrow pipe of GB300) and FP64 after.
         constexpr int BIGSYS = 512;
         __shared__ double s_red[2][NTHREADS / 32];
         auto finish = [&](CgState *st, double t0, double t1) {
@@ -744,20 +757,23 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 }
             }
         };
+        // the warp's items summed; the totals are valid in lane 0
         auto item_sums = [&](const SysEntry *e, int first, int stride, double &t0, double &t1) {
             const int nit = e->nitems;
-            double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
-            int r = 0;
-            for (int i = first; i < nit; i += stride, r = (r + 1) & 3) {
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+#pragma unroll 4
+            for (int i = first; i < nit; i += stride) {
                 if (MODE == MODE_P) {
-                    a[r] += __ldcg(e->partials + i);
+                    nsum(s0, c0, __ldcg(e->partials + i));
                 } else {
-                    a[r] += __ldcg(e->partials + nit + 2 * i);
-                    b[r] += __ldcg(e->partials + nit + 2 * i + 1);
+                    nsum(s0, c0, __ldcg(e->partials + nit + 2 * i));
+                    nsum(s1, c1, __ldcg(e->partials + nit + 2 * i + 1));
                 }
             }
-            t0 = (a[0] + a[1]) + (a[2] + a[3]);
-            t1 = (b[0] + b[1]) + (b[2] + b[3]);
+            warp_nsum(s0, c0);
+            if (MODE != MODE_P) warp_nsum(s1, c1);
+            t0 = (double)s0 + (double)c0;
+            t1 = (double)s1 + (double)c1;
         };
         // large systems: the whole block, one after the other
         for (int q = 0; q < nsys; ++q) {
@@ -766,8 +782,6 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             if (nit <= BIGSYS || *(volatile int *)&e->st->done) continue;
             double t0, t1;
             item_sums(e, threadIdx.x, NTHREADS, t0, t1);
-            t0 = warp_sum_d(t0);
-            t1 = warp_sum_d(t1);
             if (lane == 0) {
                 s_red[0][w] = t0;
                 s_red[1][w] = t1;
@@ -792,8 +806,6 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             if (nit == 0 || nit > BIGSYS || *(volatile int *)&st->done) continue;
             double t0, t1;
             item_sums(e, lane, 32, t0, t1);
-            t0 = warp_sum_d(t0);
-            t1 = warp_sum_d(t1);
             if (lane == 0) finish(st, t0, t1);
         }
     }
