@@ -977,6 +977,83 @@ __device__ __forceinline__ double oblock_sum(double v, double *sred) {
     return t;
 }
 
+// compensated FP32 sum (Neumaier): the value is s + c
+__device__ __forceinline__ void onsum(float &s, float &c, float v) {
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+// the warp's compensated pairs combined in a fixed tree (lane 0 holds them)
+__device__ __forceinline__ void owarp_nsum(float &s, float &c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+        onsum(s, c, s2);
+        c += c2;
+    }
+}
+
+// FP32 form of olast_total below: each thread brings a compensated pair per
+// value; warps, the block and then the last block over the per-block
+// partials combine them compensated in FP32, in a fixed order (the last
+// block runs alone at the end of the launch, and FP64 is a narrow pipe of
+// GB300).  The totals (FP64) are valid in thread 0 of the last block.
+template <int NT, int NV>
+__device__ bool olast_total_f(unsigned *counter, float *partials, float (&s)[NV], float (&c)[NV],
+                              double (&tot)[NV]) {
+    __shared__ float sw[NT / 32][NV][2];
+    __shared__ int s_last;
+    const int nb = gridDim.x, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    auto block_pair = [&](int v, float &bs, float &bc) {
+        bs = 0.f;
+        bc = 0.f;
+        for (int q = 0; q < NT / 32; ++q) {
+            onsum(bs, bc, sw[q][v][0]);
+            bc += sw[q][v][1];
+        }
+    };
+#pragma unroll
+    for (int v = 0; v < NV; ++v) owarp_nsum(s[v], c[v]);
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            sw[w][v][0] = s[v];
+            sw[w][v][1] = c[v];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < NV; ++v) {
+            float bs, bc;
+            block_pair(v, bs, bc);
+            partials[v * nb + blockIdx.x] = bs + bc;
+        }
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int v = 0; v < NV; ++v) {
+        float as = 0.f, ac = 0.f;
+        for (int q = threadIdx.x; q < nb; q += NT) onsum(as, ac, __ldcg(partials + v * nb + q));
+        owarp_nsum(as, ac);
+        __syncthreads();
+        if (l == 0) {
+            sw[w][v][0] = as;
+            sw[w][v][1] = ac;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float bs, bc;
+            block_pair(v, bs, bc);
+            tot[v] = (double)bs + (double)bc;
+        }
+    }
+    return true;
+}
+
 // per-block partials then the last block's fixed-order total
 template <int NT, int NV>
 __device__ bool olast_total(unsigned *counter, double *partials, const double (&mine)[NV],
@@ -1039,8 +1116,9 @@ __device__ __forceinline__ void finalize_u(CgState *s, double t0, double t1) {
 // brick's 64 threads synchronise on their own named barrier.  Only pure
 // nodes are applied here; level-transition rows go to the CSR kernel.  Bits
 // 4-5 of the code byte hold the node kind.  Dot products: FP32 within a
-// brick, compensated FP32 across a thread's bricks, FP64 across threads and
-// blocks (GB300's FP64 rate is far below its FP32 rate).
+// brick, compensated FP32 across a thread's bricks and (in the FP32 solver)
+// across threads and blocks, FP64 for the totals (GB300's FP64 rate is far
+// below its FP32 rate).
 constexpr int PX = 10;         // staged plane side (8 + 2 halo lines)
 constexpr int PP = PX * PX;    // staged plane size
 
@@ -1084,9 +1162,33 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
     T *V = sv[g];
     uint8_t *C = sc[g];
     const int q0 = (j + 1) * PX + (i + 1);  // this column's position in a staged plane
-    for (int b = blockIdx.x * 4 + g; b < nb; b += gridDim.x * 4) {
+    // x/y face halos: 4 faces x 64 values, 4 per thread; f is this thread's face
+    const int f = c >> 4;  // 0 -x, 1 +x, 2 -y, 3 +y
+    // Neighbour ids are read one brick ahead, so that every global load of a
+    // brick (own columns, face halos, z halos) issues before the first
+    // shared-memory store and the brick waits on one memory latency, not two.
+    const int bstride = gridDim.x * 4;
+    int pf_f = -1, pf_zm = -1, pf_zp = -1, pf_s = -1;
+    {
+        const int b0 = blockIdx.x * 4 + g;
+        if (b0 < nb) {
+            pf_f = t.bnbr[6 * b0 + f];
+            pf_zm = t.bnbr[6 * b0 + 4];
+            pf_zp = t.bnbr[6 * b0 + 5];
+            if (c < 6) pf_s = t.bnbr[6 * b0 + c];
+        }
+    }
+    for (int b = blockIdx.x * 4 + g; b < nb; b += bstride) {
+        const int nbk = pf_f, nzm = pf_zm, nzp = pf_zp;
         group_sync(g);  // the group's previous brick is done with its buffers
-        if (c < 6) snb[g][c] = t.bnbr[6 * b + c];
+        if (c < 6) snb[g][c] = pf_s;
+        if (b + bstride < nb) {
+            const int bn = b + bstride;
+            pf_f = t.bnbr[6 * bn + f];
+            pf_zm = t.bnbr[6 * bn + 4];
+            pf_zp = t.bnbr[6 * bn + 5];
+            if (c < 6) pf_s = t.bnbr[6 * bn + c];
+        }
         const int level = t.blow[b].w;
         T wi = 0, wo = 0, kp = 0;
         if constexpr (sizeof(T) == 4) {
@@ -1102,43 +1204,26 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
             cd[k] = A.code[base + 64 * k];
             v[k] = value(base + 64 * k, cd[k]);
             if constexpr (MODE == OM_U) {
-                // issued before the barriers so that their latency overlaps
                 xr[k] = A.x[base + 64 * k];
                 zr[k] = A.zz[base + 64 * k];
             }
-            V[k * PP + q0] = v[k];
-            C[k * PP + q0] = cd[k];
         }
-        group_sync(g);  // snb visible
-        // x/y face halos: 4 faces x 64 values, 4 per thread
-        {
-            const int f = c >> 4;  // 0 -x, 1 +x, 2 -y, 3 +y
-            const int nbk = snb[g][f];
+        T hv[4];
+        uint8_t hc[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = (c & 15) + 16 * r;
-                const int u = m & 7, k = m >> 3;
-                int sq, n;
-                if (f < 2) {
-                    sq = k * PP + (u + 1) * PX + (f == 0 ? 0 : 9);
-                    n = (k * 8 + u) * 8 + (f == 0 ? 7 : 0);
-                } else {
-                    sq = k * PP + (f == 2 ? 0 : 9) * PX + (u + 1);
-                    n = (k * 8 + (f == 2 ? 7 : 0)) * 8 + u;
-                }
-                T val = 0;
-                uint8_t cc = 0;
-                if (nbk >= 0) {
-                    n += nbk << 9;
-                    cc = A.code[n];
-                    val = value(n, cc);
-                }
-                V[sq] = val;
-                C[sq] = cc;
+        for (int r = 0; r < 4; ++r) {
+            const int m = (c & 15) + 16 * r;
+            const int u = m & 7, k = m >> 3;
+            int n = f < 2 ? (k * 8 + u) * 8 + (f == 0 ? 7 : 0) : (k * 8 + (f == 2 ? 7 : 0)) * 8 + u;
+            hv[r] = 0;
+            hc[r] = 0;
+            if (nbk >= 0) {
+                n += nbk << 9;
+                hc[r] = A.code[n];
+                hv[r] = value(n, hc[r]);
             }
         }
         // z halos of this column and the -z neighbour's code
-        const int nzm = snb[g][4], nzp = snb[g][5];
         T zm = 0, zp = 0;
         uint8_t czm = 0;
         if (nzm >= 0) {
@@ -1147,7 +1232,21 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
             zm = value(n, czm);
         }
         if (nzp >= 0) zp = value((nzp << 9) + c, A.code[(nzp << 9) + c]);
-        group_sync(g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            V[k * PP + q0] = v[k];
+            C[k * PP + q0] = cd[k];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int m = (c & 15) + 16 * r;
+            const int u = m & 7, k = m >> 3;
+            const int sq = f < 2 ? k * PP + (u + 1) * PX + (f == 0 ? 0 : 9)
+                                 : k * PP + (f == 2 ? 0 : 9) * PX + (u + 1);
+            V[sq] = hv[r];
+            C[sq] = hc[r];
+        }
+        group_sync(g);  // staged planes and snb visible
         float bs0 = 0.f, bs1 = 0.f;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -1261,21 +1360,27 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
         }
     }
     if (MODE == OM_A) return;
-    if constexpr (sizeof(T) == 4) {
-        d0 = (double)s0 - (double)c0;
-        d1 = (double)s1 - (double)c1;
-    }
-    double mine[2] = {d0, d1}, tot[2];
-    if (olast_total<OB, 2>(&A.st->counter, A.partials, mine, tot)) {
-        if (threadIdx.x == 0) {
-            CgState *s = A.st;
-            if (MODE == OM_P) {
-                finalize_p(s, tot[0]);
-            } else {
-                finalize_u(s, tot[0], tot[1]);
-            }
-            s->counter = 0;
+    auto finish = [&](const double (&tot)[2]) {
+        CgState *s = A.st;
+        if (MODE == OM_P) {
+            finalize_p(s, tot[0]);
+        } else {
+            finalize_u(s, tot[0], tot[1]);
         }
+        s->counter = 0;
+    };
+    double tot[2];
+    if constexpr (sizeof(T) == 4) {
+        // Kahan pairs (value s - c) as compensated pairs (value s + c')
+        float ps[2] = {s0, s1}, pc[2] = {-c0, -c1};
+        if (olast_total_f<OB, 2>(&A.st->counter, reinterpret_cast<float *>(A.partials), ps, pc,
+                                 tot) &&
+            threadIdx.x == 0)
+            finish(tot);
+    } else {
+        double mine[2] = {d0, d1};
+        if (olast_total<OB, 2>(&A.st->counter, A.partials, mine, tot) && threadIdx.x == 0)
+            finish(tot);
     }
 }
 
