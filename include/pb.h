@@ -228,12 +228,14 @@ pb_status pb_assemble_coeffs(pb_grid *g, const pb_params *params, void *stream,
 void pb_system_free(pb_system *s);
 
 /* pb_coulomb_terms -- analytic N-body sums of Sec. 3.3: PB_CT_SURFACE
- * computes Phi_e and Psi_e at the crossing points of flux edges; PB_CT_PAIRS
- * the Coulomb energy (both: FP32 tiled kernel with split (hi+lo)
- * coordinates and compensated sums, FP64 results); PB_CT_BOUNDARY recomputes
- * the Coulomb / Debye-Hueckel boundary values of Sec. 2.3 (FP64 kernel, so
- * that the Dirichlet lift carries no FP32 rounding).  Results stay on the
- * device inside s. */
+ * computes Phi_e and Psi_e at the crossing points of flux edges (FP32 tiled
+ * kernel with split (hi+lo) coordinates and compensated sums, FP64
+ * results); PB_CT_PAIRS the Coulomb energy sum_{i<j} q_i q_j / r_ij (FP64
+ * kernel over pairs of 128-atom tiles, summed in a fixed order: the energy
+ * is a difference of large terms of either sign; at most 1,048,576 atoms,
+ * else PB_ERR_ARG); PB_CT_BOUNDARY recomputes the Coulomb / Debye-Hueckel
+ * boundary values of Sec. 2.3 (FP64 kernel, so that the Dirichlet lift
+ * carries no FP32 rounding).  Results stay on the device inside s. */
 pb_status pb_coulomb_terms(pb_system *s, int32_t which, void *stream);
 
 /* pb_solve -- Jacobi-preconditioned CG for (G^T W G + C) phi = f (the

@@ -294,7 +294,7 @@ void pb_system_free(pb_system *s) {
     cudaStreamSynchronize(st);
     void *ptrs[] = {s->W[0], s->W[1], s->W[2], s->diag, s->rhs, s->bc, s->phi, s->code, s->w32[0], s->w32[1], s->w32[2],
                     s->z32, s->pa32, s->pb32, s->d32, s->z64, s->pa64, s->pb64, s->x64,
-                    s->partials, s->queue, s->st, s->Phi, s->Psi, s->ecoul_phi, s->eacc};
+                    s->partials, s->queue, s->st, s->Phi, s->Psi, s->eacc};
     for (void *p : ptrs) dfree(p, st);
     oct_system_free(s, st);
     cudaStreamSynchronize(st);

@@ -43,7 +43,7 @@ __global__ void k_split_atoms(const double *__restrict__ atoms, long long na, do
 }
 
 // Target kinds
-enum { TK_BOUNDARY = 0, TK_SURFACE = 1, TK_ATOMS = 2 };
+enum { TK_BOUNDARY = 0, TK_SURFACE = 1 };
 
 struct TargetDesc {
     int kind;
@@ -53,9 +53,6 @@ struct TargetDesc {
     const double *rp;
     const long long *ids;
     const int8_t *sign;
-    // atoms
-    const double *atoms;
-    long long na;
     long long count;
 };
 
@@ -123,10 +120,6 @@ __device__ __forceinline__ TgtLoad load_target(const TargetDesc &T, long long t)
             p[0] = T.rp[3 * t];
             p[1] = T.rp[3 * t + 1];
             p[2] = T.rp[3 * t + 2];
-        } else {
-            p[0] = T.atoms[t];
-            p[1] = T.atoms[T.na + t];
-            p[2] = T.atoms[2 * T.na + t];
         }
     }
     for (int d = 0; d < 3; ++d) {
@@ -275,16 +268,62 @@ k_boundary64(GridGeo g, const double *__restrict__ atoms, long long na, long lon
     if (t < count) bc[(kk * g.ny + j) * g.nx + i] = scale * acc;
 }
 
-// sum_i q_i Phi_i in a fixed order (one block) -> eacc->ecoul_sum
+// Coulomb pair sum sum_{i<j} q_i q_j / r_ij in FP64 (the energy is a
+// difference of large sums of either sign, so its terms are kept exact to
+// rounding).  Atoms in tiles of PT; block (a, b) of the nt x nt grid, a <= b,
+// takes the pairs i in tile a, j in tile b (j > i when a == b): thread t holds
+// atom i, tile b is staged in shared memory and taken in ascending order,
+// 1/r from the double-precision rsqrt.  The block's total goes to
+// part[b * nt + a] (zero for a > b); one block then adds the partials in
+// index order, so the sum is the same on every run.
+constexpr int PT = 128;
+
+__global__ void __launch_bounds__(PT)
+k_pairs64(const double *__restrict__ atoms, long long na, double *__restrict__ part) {
+    __shared__ double sx[PT], sy[PT], sz[PT], sq[PT];
+    using BR = cub::BlockReduce<double, PT>;
+    __shared__ typename BR::TempStorage tmp;
+    const int a = blockIdx.x, b = blockIdx.y, nt = gridDim.x;
+    if (a > b) {
+        if (threadIdx.x == 0) part[(long long)b * nt + a] = 0.0;
+        return;
+    }
+    const long long i = (long long)a * PT + threadIdx.x;
+    const long long j0 = (long long)b * PT, js = j0 + threadIdx.x;
+    if (js < na) {
+        sx[threadIdx.x] = atoms[js];
+        sy[threadIdx.x] = atoms[na + js];
+        sz[threadIdx.x] = atoms[2 * na + js];
+        sq[threadIdx.x] = atoms[4 * na + js];
+    }
+    __syncthreads();
+    double mine = 0.0;
+    if (i < na) {
+        const double px = atoms[i], py = atoms[na + i], pz = atoms[2 * na + i];
+        const int m = (int)min((long long)PT, na - j0);
+        const int q0 = a == b ? threadIdx.x + 1 : 0;  // j > i on the diagonal tile
+        double acc = 0.0;
+        for (int q = q0; q < m; ++q) {
+            const double dx = px - sx[q], dy = py - sy[q], dz = pz - sz[q];
+            const double r2 = (dx * dx + dy * dy) + dz * dz;
+            if (r2 > 0.0) acc += sq[q] * rsqrt(r2);
+        }
+        mine = atoms[4 * na + i] * acc;
+    }
+    const double tot = BR(tmp).Sum(mine);
+    if (threadIdx.x == 0) part[(long long)b * nt + a] = tot;
+}
+
+// 2 sum_{i<j} (the sum over i of q_i Phi_i) from the pair partials, in index
+// order -> eacc->ecoul_sum
 __global__ void __launch_bounds__(1024)
-k_reduce_qphi(const double *__restrict__ atoms, long long na, const double *__restrict__ phi,
-              EnergyAcc *eacc) {
+k_reduce_pairs(const double *__restrict__ part, long long n, EnergyAcc *eacc) {
     using BR = cub::BlockReduce<double, 1024>;
     __shared__ typename BR::TempStorage tmp;
     double s = 0.0;
-    for (long long i = threadIdx.x; i < na; i += 1024) s += atoms[4 * na + i] * phi[i];
+    for (long long i = threadIdx.x; i < n; i += 1024) s += part[i];
     double tot = BR(tmp).Sum(s);
-    if (threadIdx.x == 0) eacc->ecoul_sum = tot;
+    if (threadIdx.x == 0) eacc->ecoul_sum = 2.0 * tot;
 }
 
 pb_status split_sources(pb_system *sys, cudaStream_t s, float4 **hi, float4 **lo) {
@@ -310,8 +349,6 @@ TargetDesc make_desc(pb_system *sys, int kind) {
     T.rp = g->crp;
     T.ids = g->cid;
     T.sign = g->csign;
-    T.atoms = g->atoms;
-    T.na = g->na;
     T.count = 0;
     return T;
 }
@@ -355,25 +392,23 @@ pb_status nbody_surface(pb_system *sys, cudaStream_t s) {
 
 pb_status nbody_pairs(pb_system *sys, cudaStream_t s) {
     pb_grid *g = sys->g;
-    long long na = g->na > 0 ? g->na : 1;
-    if (!sys->ecoul_phi) sys->ecoul_phi = (double *)dalloc(sizeof(double) * na, s);
-    if (!sys->ecoul_phi) return PB_ERR_OOM;
-    if (g->na == 0) {
+    if (g->na <= 1) {
         PB_CUDA_TRY(cudaMemsetAsync(&sys->eacc->ecoul_sum, 0, sizeof(double), s));
         return PB_OK;
     }
-    float4 *hi, *lo;
-    pb_status st = split_sources(sys, s, &hi, &lo);
-    if (st != PB_OK) return st;
-    TargetDesc T = make_desc(sys, TK_ATOMS);
-    T.count = g->na;
-    k_nbody<false, false><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
-        T, hi, lo, g->na, 0.f, 1.0, sys->ecoul_phi, nullptr);
+    const long long nt = cdiv(g->na, PT);
+    if (nt > 8192) {  // the partials grow as nt^2 (512 MB at this limit)
+        set_error("too many atoms for the Coulomb pair sum (%lld; at most %d)",
+                  (long long)g->na, 8192 * PT);
+        return PB_ERR_ARG;
+    }
+    double *part = (double *)dalloc(sizeof(double) * nt * nt, s);
+    if (!part) return PB_ERR_OOM;
+    k_pairs64<<<dim3((unsigned)nt, (unsigned)nt), PT, 0, s>>>(g->atoms, g->na, part);
     PB_LAUNCH_CHECK();
-    k_reduce_qphi<<<1, 1024, 0, s>>>(g->atoms, g->na, sys->ecoul_phi, sys->eacc);
+    k_reduce_pairs<<<1, 1024, 0, s>>>(part, nt * nt, sys->eacc);
     PB_LAUNCH_CHECK();
-    dfree(hi, s);
-    dfree(lo, s);
+    dfree(part, s);
     return PB_OK;
 }
 

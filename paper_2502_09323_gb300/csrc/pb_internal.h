@@ -190,7 +190,6 @@ struct pb_system {
     pbg::CgState *st;
     pbg::CgState *h_st; // pinned host mirror
     double *Phi, *Psi;  // [ncross]
-    double *ecoul_phi;  // [na] Phi at atoms (self excluded)
     pbg::EnergyAcc *eacc;
     pb_energy_terms *h_energy;  // pinned
     int solved, have_surface, have_pairs;
