@@ -225,10 +225,13 @@ __global__ void __launch_bounds__(OT) k_oct_bbox(const double *__restrict__ atom
 }
 
 // near flag of every level-l box (children of boxes that are not near are
-// not near either)
+// not near either).  Only an atom whose centre lies within reach = R_max +
+// dist of the box can pass the test, so the box scans the atom cell list
+// over the cells that meet the box grown by reach (one cell of margin on
+// each side); the flag is an OR over atoms, so the order does not matter.
 __global__ void k_oct_near(const double *__restrict__ atoms, long long na, OctDev t, int level,
-                           double dist, const uint8_t *__restrict__ parent_near,
-                           uint8_t *__restrict__ near) {
+                           double dist, double reach, CellList cl,
+                           const uint8_t *__restrict__ parent_near, uint8_t *__restrict__ near) {
     const int nl = t.n0 << level;
     const long long nbox = (long long)nl * nl * nl;
     const long long q = blockIdx.x * (long long)OT + threadIdx.x;
@@ -249,8 +252,24 @@ __global__ void k_oct_near(const double *__restrict__ atoms, long long na, OctDe
         b[d] = wpos(t, d, lo[d] + side);
     }
     const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
+    int c0[3], c1[3];
+    bool empty = false;
+    for (int d = 0; d < 3; ++d) {
+        double u0 = floor((a[d] - reach - cl.lo[d]) / cl.cs) - 1.0;
+        double u1 = floor((b[d] + reach - cl.lo[d]) / cl.cs) + 1.0;
+        u0 = fmax(u0, 0.0);
+        u1 = fmin(u1, (double)cl.dim[d] - 1.0);
+        if (!(u0 <= u1)) empty = true;
+        c0[d] = empty ? 0 : (int)u0;
+        c1[d] = empty ? -1 : (int)u1;
+    }
     uint8_t hit = 0;
-    for (long long i = 0; i < na && !hit; ++i) {
+    for (int cz = c0[2]; cz <= c1[2] && !hit && !empty; ++cz)
+    for (int cy = c0[1]; cy <= c1[1] && !hit; ++cy)
+    for (int cx = c0[0]; cx <= c1[0] && !hit; ++cx) {
+    const int cid = (cz * cl.dim[1] + cy) * cl.dim[0] + cx;
+    for (int sidx = cl.start[cid]; sidx < cl.start[cid + 1] && !hit; ++sidx) {
+        const int i = cl.atom[sidx];
         const double c[3] = {X[i], Y[i], Z[i]};
         double tt[3], u[3];
         for (int d = 0; d < 3; ++d) {
@@ -264,6 +283,7 @@ __global__ void k_oct_near(const double *__restrict__ atoms, long long na, OctDe
         const double rin = __dmul_rn(R[i] + dist, R[i] + dist);
         const double ro = R[i] - dist;
         if (dmin2 <= rin && (ro <= 0.0 || dmax2 >= __dmul_rn(ro, ro))) hit = 1;
+    }
     }
     near[q] = hit;
 }
@@ -1632,6 +1652,7 @@ pb_status oct_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
         split[l] = (uint8_t *)dalloc(nl * nl * nl, s);
         if (!near[l] || !split[l]) return PB_ERR_OOM;
         k_oct_near<<<cdiv(nl * nl * nl, OT), OT, 0, s>>>(g->atoms, na, t, l, dist,
+                                                          hinfo.rmax + dist, g->cells,
                                                           l > 0 ? near[l - 1] : nullptr, near[l]);
         PB_LAUNCH_CHECK();
         np.p[l] = near[l];
