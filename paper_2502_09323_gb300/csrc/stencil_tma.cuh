@@ -6,10 +6,9 @@
 // 128 x 8 tile column of one system -- from a global atomic counter.  The
 // producer announces each chunk in a small descriptor ring before arming the
 // chunk's first plane, so consumers learn it through the same mbarrier; the
-// TMA pipeline keeps streaming across chunks and systems.  Each item's dot
-// products go to that item's own slot; the block that finishes a system's
-// last item sums the system's slots in item order and updates its CG state,
-// so every result is independent of scheduling and of the other systems.  One producer warp (lane 0) issues, for every plane, tensor-map
+// TMA pipeline keeps streaming across chunks and systems.
+//
+// One producer warp (lane 0) issues, for every plane, tensor-map
 // (cp.async.bulk.tensor) loads of
 //   * the streamed vector on a 136 x 10 box (4 columns of x halo on each side
 //     and one halo row above and below; out-of-range elements are zero),
@@ -20,7 +19,18 @@
 // The 8 consumer warps compute one row each; a warp holds at most two slots
 // (planes k and k+1) and keeps its own row of planes k-1, k in registers, so
 // the producer runs up to NSLOT-2 planes ahead of the slowest warp.  No
-// consumer ever waits on another consumer.
+// consumer ever waits on another consumer.  Rows without listed edges take
+// a packed FP32x2 fast path; rows with listed edges gather their weights
+// (the update kernel prefetches the next plane's into L1).
+//
+// Dot products: each item's go to that item's own FP32 slot; the last block
+// of the launch sums every system's slots in an order fixed by its item
+// count (compensated FP32, FP64 for the total) and updates its CG state, so
+// every result is independent of scheduling and of the other systems.
+//
+// A one-system launch may overlap the previous kernel of its stream
+// (programmatic dependent launch): every read of data that kernel wrote
+// comes after griddepcontrol.wait.
 //
 // Every wait is bounded: after TMA_WAIT_LIMIT polls a wait gives up, the
 // block records status 3 in the solver state, stops, waits (bounded) for its
