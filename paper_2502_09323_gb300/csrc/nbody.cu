@@ -10,6 +10,11 @@
 // contributions are summed with Kahan compensation in FP32 and the tile sum
 // is added to an FP64 accumulator.  A thread's two targets share each
 // instruction through the packed FP32x2 arithmetic of sm_100-class GPUs.
+// It serves the surface terms Phi_p, Psi_p at the crossing points.
+//
+// FP64 kernels: the boundary values (they enter the linear system) and the
+// Coulomb energy sum_{i<j} q_i q_j / r_ij (a net value of large terms of
+// either sign), each summed in a fixed order.
 #include <cub/block/block_reduce.cuh>
 
 #include "pb_internal.h"
