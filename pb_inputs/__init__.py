@@ -96,6 +96,34 @@ def born_ion() -> np.ndarray:
     return np.array([[10.0, 10.0, 10.0, 2.0, 1.0]])
 
 
+def lattice_balls() -> np.ndarray:
+    """Balls placed on the lattice of spacing 0.5 from (-8, -8, -8): surfaces
+    through nodes (interval ends exactly at 0 or 1), spheres tangent to
+    lattice lines, a chord inside one edge, nested and abutting balls, and
+    two partial intervals whose union is a whole edge."""
+    return np.array([
+        [0.0, 0.0, 0.0, 2.0, 1.0],      # centre on a node, R = 4h
+        [0.0, 0.0, 0.0, 1.0, 0.0],      # nested, same centre
+        [3.0, 0.0, 0.0, 1.0, -1.0],     # touches the first at the node x = 2
+        [-4.0, 2.75, 1.0, 0.25, 0.5],   # tangent to the lines y = 2.5 and 3.0 at z = 1
+        [5.25, 5.0, 5.0, 0.2, 0.0],     # chord [5.05, 5.45] inside the edge [5, 5.5]
+        [-5.0, -5.0, 4.0, 0.65, 0.3],   # covers [-5.5, -5.0] and part of [-4.5, -4.0] ...
+        [-4.0, -5.0, 4.0, 0.55, 0.0],   # ... and this one the rest of it
+        [4.0, -4.0, -4.0, 1.5, -0.5],   # centre on a node, R = 3h
+        [4.25, -4.25, -3.75, 0.75, 0.0],  # centre at a cell centre
+    ])
+
+
+def snapped_molecule(n_atoms: int = 80, seed: int = 104) -> np.ndarray:
+    """A globular molecule centred on the origin with coordinates rounded to
+    multiples of 0.125 and radii to multiples of 0.25 (at least 0.5): on the
+    lattice of spacing 0.5 its spheres meet nodes and lines exactly."""
+    atoms = globular_molecule(n_atoms, seed=seed)
+    atoms[:, :3] = np.round((atoms[:, :3] - atoms[:, :3].mean(0)) / 0.125) * 0.125
+    atoms[:, 3] = np.maximum(np.round(atoms[:, 3] / 0.25) * 0.25, 0.5)
+    return atoms
+
+
 def batch_sizes(count: int, seed_base: int, lo: int, hi: int) -> np.ndarray:
     """Atom counts log-uniform in [lo, hi] for a batch of ``count`` molecules."""
     rng = np.random.Generator(np.random.PCG64(seed_base))

@@ -87,36 +87,13 @@ def test_crossing_list_bit_exact(pb, case):
     assert g.info.n_flux == int((cr["sign"] != 0).sum())
 
 
-def _lattice_balls():
-    """Balls placed on the lattice of h = 0.5 from (-8, -8, -8): surfaces
-    through nodes (intervals ending exactly at t = 0 or 1), spheres tangent to
-    lattice lines (s = 0), chords inside one edge, nested and abutting balls,
-    and two partial intervals whose union is the whole edge."""
-    return np.array([
-        [0.0, 0.0, 0.0, 2.0, 1.0],      # centre on a node, R = 4h
-        [0.0, 0.0, 0.0, 1.0, 0.0],      # nested, same centre
-        [3.0, 0.0, 0.0, 1.0, -1.0],     # touches the first at the node x = 2
-        [-4.0, 2.75, 1.0, 0.25, 0.5],   # tangent to the lines y = 2.5 and 3.0 at z = 1
-        [5.25, 5.0, 5.0, 0.2, 0.0],     # chord [5.05, 5.45] inside the edge [5, 5.5]
-        [-5.0, -5.0, 4.0, 0.65, 0.3],   # covers [-5.5, -5.0] and part of [-4.5, -4.0] ...
-        [-4.0, -5.0, 4.0, 0.55, 0.0],   # ... and this one the rest of it
-        [4.0, -4.0, -4.0, 1.5, -0.5],   # centre on a node, R = 3h
-        [4.25, -4.25, -3.75, 0.75, 0.0],  # centre at a cell centre
-    ])
-
-
 @pytest.mark.parametrize("kind", ["placed", "snapped"])
 def test_crossing_list_degenerate_geometry(pb, orc, kind):
     """Classification and crossing list bit-exact on inputs full of exact
     ties; the snapped molecule has coordinates on multiples of h/4 and radii
     on multiples of h/2."""
     h = 0.5
-    if kind == "placed":
-        atoms = _lattice_balls()
-    else:
-        atoms = pb_inputs.globular_molecule(80, seed=104)
-        atoms[:, :3] = np.round((atoms[:, :3] - atoms[:, :3].mean(0)) / 0.125) * 0.125
-        atoms[:, 3] = np.maximum(np.round(atoms[:, 3] / 0.25) * 0.25, 0.5)
+    atoms = pb_inputs.lattice_balls() if kind == "placed" else pb_inputs.snapped_molecule()
     og = orc.Grid((33, 33, 33), (-8.0, -8.0, -8.0), h)
     g = pb.pb_build_grid(pb.GridSpec(n=(33, 33, 33), origin=(-8.0, -8.0, -8.0), h=h), atoms)
     inside = orc.classify(og, atoms)
