@@ -227,6 +227,12 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
     // as SMs free up; it waits the same way before touching our results.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // A one-system launch issued after its solve finished (the host polls
+    // with launches in flight) does nothing: every block leaves before
+    // touching the work counters, which the last launch left at zero.  The
+    // done flag changes only between launches, so all blocks agree.
+    if constexpr (SINGLE)
+        if (MODE != MODE_A && *(volatile int *)&e0.st->done) return;
     if (threadIdx.x == 0) {
         s_nsys = nsys < 0 ? (int)((volatile unsigned int *)queue)[2] : nsys;
         s_total = nsys < 0 ? (int)((volatile unsigned int *)queue)[3] : total_items;
