@@ -39,18 +39,25 @@ import scipy.special as sp
 
 def _real_ylm(L: int, theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
     """Real orthonormal spherical harmonics, rows (n, m) for n <= L in the
-    order (0,0), (1,-1), (1,0), (1,1), ...; columns the points."""
+    order (0,0), (1,-1), (1,0), (1,1), ...; columns the points.  Built from
+    the associated Legendre functions: sqrt((2n+1)/(4 pi) (n-|m|)!/(n+|m|)!)
+    P_n^|m|(cos theta), times sqrt(2) cos(m phi) for m > 0 and sqrt(2)
+    sin(|m| phi) for m < 0."""
+    x = np.cos(theta)
     out = np.empty(((L + 1) ** 2, theta.size))
     row = 0
     for n in range(L + 1):
         for m in range(-n, n + 1):
-            y = sp.sph_harm_y(n, abs(m), theta, phi)
+            am = abs(m)
+            norm = math.sqrt((2 * n + 1) / (4.0 * math.pi) *
+                             math.exp(math.lgamma(n - am + 1) - math.lgamma(n + am + 1)))
+            p = sp.lpmv(am, n, x)
             if m > 0:
-                out[row] = math.sqrt(2.0) * (-1) ** m * y.real
+                out[row] = math.sqrt(2.0) * norm * p * np.cos(am * phi)
             elif m < 0:
-                out[row] = math.sqrt(2.0) * (-1) ** m * y.imag
+                out[row] = math.sqrt(2.0) * norm * p * np.sin(am * phi)
             else:
-                out[row] = y.real
+                out[row] = norm * p
             row += 1
     return out
 
