@@ -110,3 +110,24 @@ def test_a_request_above_the_budget_is_refused():
         assert "above the budget" in str(e)
     else:
         raise AssertionError("expected a refusal")
+
+
+def test_octree_estimate_covers_the_transient_lattice_and_grows():
+    """The octree estimate includes the build's finest-lattice pass (an inside
+    byte per node and two bytes per edge, freed after the build) and grows
+    with the molecule and with a finer finest level."""
+    import math
+    small = pb_inputs.globular_molecule(500, seed=6)
+    big = pb_inputs.globular_molecule(4000, seed=7)
+    for atoms in (small, big):
+        spec = serving.octree_spec(atoms, h_fine=0.25)
+        lo = (atoms[:, :3] - atoms[:, 3:4]).min(0)
+        hi = (atoms[:, :3] + atoms[:, 3:4]).max(0)
+        n0 = max(1, math.ceil(spec.fill * float((hi - lo).max()) / (8.0 * spec.h_bulk)))
+        lattice = (n0 * 8.0 * spec.h_bulk / spec.h_fine + 1) ** 3
+        assert serving.device_bytes_estimate(spec, len(atoms), atoms) > 7 * lattice
+    e_small = serving.device_bytes_estimate(serving.octree_spec(small), len(small), small)
+    e_big = serving.device_bytes_estimate(serving.octree_spec(big), len(big), big)
+    assert e_big > e_small
+    coarse = serving.device_bytes_estimate(serving.octree_spec(big, h_fine=0.5), len(big), big)
+    assert e_big > coarse
