@@ -50,6 +50,51 @@ def _dense_operator(orc, g, coef):
 
 
 # --------------------------------------------------------------------------
+# grid placement (perfil, Sec. 2.3 and Sec. 3.4)
+# --------------------------------------------------------------------------
+
+# Three balls chosen by hand.  Their union spans x in [-1, 6], y in [-1, 5.5]
+# and z in [-4, 3.5]: the largest span (7.5) is along z, the low and high
+# ends of each axis come from different balls, and the centres alone span
+# only 4, 5 and 5.  Every number below is exact in binary, so placement is
+# checked for equality.
+_PLACE_ATOMS = np.array([[0.0, 0.0, 0.0, 1.0, 0.5],
+                         [4.0, 1.0, -2.0, 2.0, -0.3],
+                         [1.0, 5.0, 3.0, 0.5, 0.1]])
+
+
+def test_uniform_placement_by_hand(orc):
+    """Cube of side fill * extent (extent = largest axis span of the union of
+    the balls) centred on the balls' bounding box, with h = L / (n - 1): here
+    L = 1.5 * 7.5 = 11.25, h = 11.25 / 9 = 1.25 and the box centre is
+    (2.5, 2.25, -0.25).  Taking the extent over the centres (L = 7.5), the
+    spacing as L / n (1.125), or the centroid of the atoms as the centre
+    would each change the result."""
+    g = orc.place_grid(_PLACE_ATOMS, 10, 1.5)
+    assert tuple(int(v) for v in g.n) == (10, 10, 10)
+    assert g.h == 1.25
+    assert tuple(g.origin) == (-3.125, -3.375, -5.875)
+    # the far corner is the box centre plus L/2 on every axis
+    far = np.asarray(g.origin) + 9 * g.h
+    assert tuple(far) == (8.125, 7.875, 5.375)
+
+
+def test_octree_placement_by_hand(orc):
+    """The octree domain is n0 coarse bricks of side 8 h_bulk per axis, with
+    n0 = ceil(fill * extent / (8 h_bulk)), centred on the same bounding box:
+    1.5 * 7.5 / 8 = 1.40625 gives n0 = 2 (side 16 at h_bulk = 1) and
+    0.5 * 7.5 / 8 gives n0 = 1 (side 8); at h_bulk = 0.25 it is
+    ceil(11.25 / 2) = 6 (side 12)."""
+    from oracle import octree
+    for h_bulk, fill, n0, side in ((1.0, 1.5, 2, 16.0), (1.0, 0.5, 1, 8.0),
+                                   (0.25, 1.5, 6, 12.0)):
+        origin, got = octree.place(_PLACE_ATOMS, h_bulk, fill)
+        assert got == n0
+        centre = np.array([2.5, 2.25, -0.25])
+        assert np.array_equal(origin, centre - side / 2)
+
+
+# --------------------------------------------------------------------------
 # units and closed forms
 # --------------------------------------------------------------------------
 
