@@ -343,6 +343,19 @@ pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int
  * autotuner's choice (which times the candidates on first use of a shape). */
 pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_t z_chunk);
 
+/* pb_set_wait_limit -- failure-injection hook for tests: the number of polls
+ * after which a ring-slot wait of the FP32 PCG kernels (one-system, batched
+ * and served launches) gives up; polls < 0 restores the default (2^20).  With
+ * 0 every slot wait gives up at once, so the next FP32 PCG launch stops, waits
+ * for its own copies in flight and marks every system of its launch with
+ * device status 3: pb_solve and pb_solve_batch then return PB_ERR_TIMEOUT, and
+ * a served system finishes with that status.  The drain of a block's own
+ * copies keeps the default limit, and the work counters are reset as after any
+ * launch, so the system solves normally once the limit is restored.  Applies
+ * to the current device; synchronises the device, so call it with no solve in
+ * flight.  The paper has no counterpart (it covers failure detection). */
+pb_status pb_set_wait_limit(int64_t polls);
+
 /* pb_apply_dot_noalloc -- y = A x (FP64 operator, interior nodes; boundary
  * entries of x read as zero, y = 0 on boundary nodes) and *xAx = x.(A x),
  * computed without allocating any device memory.  The paper has no

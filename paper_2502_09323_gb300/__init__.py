@@ -28,7 +28,7 @@ __all__ = [
     "GridSpec", "OctreeSpec", "Params", "SolveOpts", "Grid", "System",
     "pb_build_grid", "pb_assemble_coeffs", "pb_coulomb_terms", "pb_solve", "pb_energy",
     "pb_get_array", "pb_get_phi", "pb_apply", "pb_solve_batch", "pb_last_error",
-    "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning",
+    "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning", "pb_set_wait_limit",
     "solve_molecule", "library_path", "loaded", "PBError", "Engine",
 ]
 
@@ -340,12 +340,19 @@ def pb_apply(system: System, x, precision: int = FP64, stream=None):
     return y
 
 
-def pb_solve_batch(systems, opts: SolveOpts, stream=None) -> list:
+def pb_solve_batch(systems, opts: SolveOpts, stream=None, check=True) -> list:
+    """Per-system statistics dicts (each with the call's return code under
+    ``rc``); raises on error when ``check``."""
     n = len(systems)
     arr = (C.c_void_p * n)(*[s.handle for s in systems])
     stats = (N.SolveStatsC * n)()
-    N.check(N.lib().pb_solve_batch(arr, n, C.byref(opts.c()), _stream(stream), stats))
-    return [N.struct_dict(s) for s in stats]
+    rc = N.lib().pb_solve_batch(arr, n, C.byref(opts.c()), _stream(stream), stats)
+    if check:
+        N.check(rc)
+    out = [N.struct_dict(s) for s in stats]
+    for d in out:
+        d["rc"] = rc
+    return out
 
 
 class Engine:
@@ -421,6 +428,11 @@ def pb_profile_kernels(system: System, precision: int, which: int, reps: int, st
 
 def pb_set_tuning(system: System, precision: int, variant: int, z_chunk: int) -> None:
     N.check(N.lib().pb_set_tuning(system.handle, int(precision), int(variant), int(z_chunk)))
+
+
+def pb_set_wait_limit(polls: int) -> None:
+    """Polls before an FP32 PCG ring-slot wait gives up (< 0: the default)."""
+    N.check(N.lib().pb_set_wait_limit(int(polls)))
 
 
 def pb_kernel_launches() -> int:

@@ -294,6 +294,7 @@ void pb_system_free(pb_system *s) {
     cudaStreamSynchronize(st);
     void *ptrs[] = {s->W[0], s->W[1], s->W[2], s->diag, s->rhs, s->bc, s->phi, s->code, s->w32[0], s->w32[1], s->w32[2],
                     s->z32, s->pa32, s->pb32, s->d32, s->z64, s->pa64, s->pb64, s->x64,
+                    s->r64, s->q64, s->op64[0], s->op64[1], s->op64[2], s->op64[3], s->op64[4],
                     s->partials, s->queue, s->st, s->Phi, s->Psi, s->eacc};
     for (void *p : ptrs) dfree(p, st);
     oct_system_free(s, st);
@@ -421,7 +422,8 @@ pb_status pb_solve(pb_system *s, const pb_solve_opts *opts, double *phi_dev, voi
     cudaStream_t st = (cudaStream_t)stream;
     rc = s->g->is_oct ? oct_solve(s, opts, st, stats) : solve(s, opts, st, stats);
     if (rc == PB_ERR_NOCONV) set_error("solver stopped before reaching rtol");
-    if (rc == PB_ERR_TIMEOUT) set_error("solver exceeded its time budget");
+    // a device-side wait limit reports its own message
+    if (rc == PB_ERR_TIMEOUT && !g_err[0]) set_error("solver exceeded its time budget");
     if ((rc == PB_OK || rc == PB_ERR_NOCONV) && phi_dev) {
         PB_CUDA_TRY(cudaMemcpyAsync(phi_dev, s->phi, sizeof(double) * s->g->geo.N,
                                     cudaMemcpyDeviceToDevice, st));
@@ -594,7 +596,7 @@ pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_op
     if (opts->precision == PB_MIXED) {
         pb_status r = solve_batch(systems, n, opts, (cudaStream_t)stream, stats);
         if (r == PB_ERR_NOCONV) set_error("a system stopped before reaching rtol");
-        if (r == PB_ERR_TIMEOUT) set_error("the batch exceeded its time budget");
+        if (r == PB_ERR_TIMEOUT && !g_err[0]) set_error("the batch exceeded its time budget");
         return r;
     }
     // FP64: one plain PCG after the other
@@ -706,6 +708,11 @@ pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_
         return PB_ERR_UNIMPL;
     }
     return set_tuning(s, precision, variant, z_chunk);
+}
+
+pb_status pb_set_wait_limit(int64_t polls) {
+    set_error("");
+    return set_wait_limit((long long)polls);
 }
 
 }  // extern "C"

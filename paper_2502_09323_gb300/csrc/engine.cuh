@@ -202,12 +202,16 @@ bool engine_install(Engine *e, int q) {
     return true;
 }
 
-// queue slot q's refinement step after an inner solve ended
-bool engine_refine(Engine *e, int q) {
+// queue slot q's refinement step after an inner solve ended; aborted: the
+// inner solve was stopped by a device-side wait limit (status 3), so its
+// incomplete correction is not promoted (k_ir_step then ends the solve)
+bool engine_refine(Engine *e, int q, bool aborted) {
     HostSlot &hs = e->slots[q];
     pb_system *sys = hs.job.sys;
     const GridGeo &g = sys->g->geo;
-    if (hs.job.oct) {
+    if (aborted) {
+        // no promotion
+    } else if (hs.job.oct) {
         if (oct_engine_promote(sys, e->cs) != PB_OK) {
             engine_fail(e, "promotion", cudaGetLastError());
             return false;
@@ -330,7 +334,7 @@ bool engine_process(Engine *e, int mb, bool *changed) {
             engine_complete(e, q, ms);
             *changed = true;
         } else if (ms.st.done) {
-            if (!engine_refine(e, q)) return false;
+            if (!engine_refine(e, q, ms.st.status == 3)) return false;
         }
     }
     return true;

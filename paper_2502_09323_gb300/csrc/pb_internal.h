@@ -185,6 +185,8 @@ struct pb_system {
     float *z32, *pa32, *pb32, *d32;
     // FP64 plain solver workspace (padded layout)
     double *z64, *pa64, *pb64, *x64;
+    double *r64, *q64;  // plain FP64 solver: residual and q = A p (padded)
+    double *op64[5];    // plain FP64 solver: padded +x/+y/+z weights, diagonal, 1/diagonal
     double *partials;   // reduction partials
     int npartials;
     pbg::CgState *st;
@@ -221,6 +223,7 @@ pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s);
 pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cudaStream_t s);
 void free_tma_state(pb_system *sys);
 pb_status set_tuning(pb_system *sys, int precision, int variant, int kc);
+pb_status set_wait_limit(long long polls);
 pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, cudaStream_t s,
                       pb_solve_stats *stats);
 pb_status engine_create(int device, int capacity, const pb_solve_opts *o, pb_engine **out);

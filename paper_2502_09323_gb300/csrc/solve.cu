@@ -495,11 +495,13 @@ k_stencil(KArgs<T> A, CP cp) {
 }
 
 #include "stencil_tma.cuh"
+#include "cg64.cuh"
 
 // FP64 true residual r = f - A phi on interior nodes (boundary neighbours
 // read their Dirichlet value through the lift already in f, so they are
-// masked here).  Writes z = r/diag to the padded solver layout (FP32 or FP64)
-// and reduces |r|^2 and r.z.  Persistent grid (the blocks resident on the
+// masked here).  Writes z = r/diag to the padded solver layout (FP32 or FP64),
+// and r itself when rout is given (the plain FP64 solver keeps r), and
+// reduces |r|^2 and r.z.  Persistent grid (the blocks resident on the
 // GPU): the stencil is the only FP64 arithmetic per node; for the FP32 solver
 // |r|^2 and r.z are summed in FP32 per thread and per block (they serve as
 // stopping norms and as the restart rho of the FP32 PCG) and in FP64 across
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(256)
 k_residual(const double *__restrict__ phi, const double *__restrict__ f,
            const double *__restrict__ Wx, const double *__restrict__ Wy,
            const double *__restrict__ Wz, const double *__restrict__ diag, GridGeo g, PadGeo pg,
-           TZ *__restrict__ zout, CgState *st, double *partials) {
+           TZ *__restrict__ zout, CgState *st, double *partials, double *__restrict__ rout) {
     __shared__ double sred[8];
     __shared__ TZ sblk[2][8];
     const long long stride = (long long)gridDim.x * 256;
@@ -548,6 +550,7 @@ k_residual(const double *__restrict__ phi, const double *__restrict__ f,
             z = (TZ)(r / diag[a]);
         }
         zout[(k * g.ny + j) * pg.sx + i] = z;
+        if (rout) rout[(k * g.ny + j) * pg.sx + i] = r;
         rr += rt * rt;
         rz += rt * z;
     }
@@ -920,6 +923,52 @@ pb_status launch_iter(pb_system *sys, const CP &cp, const T *z, const T *pold, T
     return PB_OK;
 }
 
+// one plain FP64 PCG iteration (direction + update kernels); cur selects
+// which of pa/pb holds p_old; which: 0 direction only, 1 update only, 2 both
+void launch_iter_cg64(pb_system *sys, int cur, int KC, cudaStream_t s, int which = 2) {
+    const PadGeo &g = sys->pad;
+    double *pbuf[2] = {sys->pa64, sys->pb64};
+    cg64::DirArgs d{};
+    d.z = sys->z64;
+    d.pold = pbuf[cur];
+    d.p = pbuf[cur ^ 1];
+    d.q = sys->q64;
+    d.w0 = sys->op64[0];
+    d.w1 = sys->op64[1];
+    d.w2 = sys->op64[2];
+    d.dg = sys->op64[3];
+    d.st = sys->st;
+    d.partials = sys->partials;
+    d.g = g;
+    d.KC = KC;
+    const dim3 grid((unsigned)cdiv(g.nx - 1, cg64::TXP), (unsigned)cdiv(g.ny - 2, cg64::WARPS),
+                    (unsigned)cdiv(g.nz - 2, KC));
+    if (which != 1) k_cg64_dir<<<grid, cg64::NT, 0, s>>>(d);
+    if (which == 0) return;
+    cg64::UpdArgs u{};
+    u.x = sys->x64;
+    u.r = sys->r64;
+    u.z = sys->z64;
+    u.p = pbuf[cur ^ 1];
+    u.q = sys->q64;
+    u.dinv = sys->op64[4];
+    u.st = sys->st;
+    u.partials = sys->partials;
+    u.first = g.sxy;
+    u.count = (long long)(g.nz - 2) * g.sxy;
+    static int per_sm = 0;
+    if (!per_sm &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg64_upd, cg64::UNT, 0) != cudaSuccess ||
+         per_sm <= 0)) {
+        cudaGetLastError();
+        per_sm = 4;
+    }
+    // partials holds two slots per block
+    const long long blocks = std::min<long long>(
+        std::min<long long>(cdiv(u.count / 2, cg64::UNT), (long long)per_sm * num_sms()), sys->npartials / 2);
+    k_cg64_upd<<<(unsigned)blocks, cg64::UNT, 0, s>>>(u);
+}
+
 double now_s() {
     using namespace std::chrono;
     return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -951,11 +1000,11 @@ pb_status residual(pb_system *sys, bool fp32_out, cudaStream_t s) {
     if (fp32_out)
         k_residual<float><<<blocks, 256, 0, s>>>(sys->phi, sys->rhs, sys->W[0], sys->W[1], sys->W[2],
                                                  sys->diag, g, sys->pad, sys->z32, sys->st,
-                                                 sys->partials);
+                                                 sys->partials, nullptr);
     else
         k_residual<double><<<blocks, 256, 0, s>>>(sys->phi, sys->rhs, sys->W[0], sys->W[1],
                                                   sys->W[2], sys->diag, g, sys->pad, sys->z64,
-                                                  sys->st, sys->partials);
+                                                  sys->st, sys->partials, sys->r64);
     PB_LAUNCH_CHECK();
     return PB_OK;
 }
@@ -981,7 +1030,7 @@ pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC
                 else
                     launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
             } else {
-                launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
+                launch_iter_cg64(sys, cur, KC, s);
             }
             cur ^= 1;
         }
@@ -1083,9 +1132,7 @@ void tune_iter(pb_system *sys, int precision, int variant, int kc, int r, cudaSt
             launch_iter<float, CoefC32>(sys, cp, sys->z32, (r & 1) ? sys->pb32 : sys->pa32,
                                         (r & 1) ? sys->pa32 : sys->pb32, sys->d32, sys->z32, kc, s);
     } else {
-        CoefS64 cp = make_s64(sys);
-        launch_iter<double, CoefS64>(sys, cp, sys->z64, (r & 1) ? sys->pb64 : sys->pa64,
-                                     (r & 1) ? sys->pa64 : sys->pb64, sys->x64, sys->z64, kc, s);
+        launch_iter_cg64(sys, r & 1, kc, s);
     }
     note_launch(2);
 }
@@ -1191,6 +1238,14 @@ pb_status set_tuning(pb_system *sys, int precision, int variant, int kc) {
     return PB_OK;
 }
 
+pb_status set_wait_limit(long long polls) {
+    const long long v = polls < 0 ? tma::TMA_WAIT_LIMIT : polls;
+    PB_CUDA_TRY(cudaDeviceSynchronize());
+    PB_CUDA_TRY(cudaMemcpyToSymbol(tma::g_slot_wait_limit, &v, sizeof(v)));
+    PB_CUDA_TRY(cudaDeviceSynchronize());
+    return PB_OK;
+}
+
 // work counters of the TMA stencil kernels ([0] next item, [1] finished
 // blocks); zero between launches because each launch's last block resets them
 pb_status ensure_queue(pb_system *sys, cudaStream_t s) {
@@ -1240,6 +1295,21 @@ pb_status ensure_solver_ws(pb_system *sys, int precision, cudaStream_t s) {
         PB_CUDA_TRY(cudaMemsetAsync(sys->pa64, 0, bytes64, s));
         PB_CUDA_TRY(cudaMemsetAsync(sys->pb64, 0, bytes64, s));
         PB_CUDA_TRY(cudaMemsetAsync(sys->x64, 0, bytes64, s));
+    }
+    if (precision == PB_FP64 && !sys->r64 && !sys->g->is_oct) {
+        // the plain solver keeps r and q, and a padded copy of the operator
+        sys->r64 = (double *)dalloc(bytes64, s);
+        sys->q64 = (double *)dalloc(bytes64, s);
+        for (int a = 0; a < 5; ++a) sys->op64[a] = (double *)dalloc(bytes64, s);
+        if (!sys->r64 || !sys->q64 || !sys->op64[0] || !sys->op64[1] || !sys->op64[2] ||
+            !sys->op64[3] || !sys->op64[4])
+            return PB_ERR_OOM;
+        PB_CUDA_TRY(cudaMemsetAsync(sys->r64, 0, bytes64, s));
+        PB_CUDA_TRY(cudaMemsetAsync(sys->q64, 0, bytes64, s));
+        k_cg64_operator<<<cdiv(p.Np, 256), 256, 0, s>>>(sys->W[0], sys->W[1], sys->W[2], sys->diag,
+                                                         sys->g->geo, p, sys->op64[0], sys->op64[1],
+                                                         sys->op64[2], sys->op64[3], sys->op64[4]);
+        PB_LAUNCH_CHECK();
     }
     return PB_OK;
 }
@@ -1291,8 +1361,11 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
             rc = run_pcg<float, CoefC32>(sys, cp, sys->z32, sys->pa32, sys->pb32, sys->d32, tune.kc,
                                          tune.variant, chunk, deadline, s, &it);
             if (rc == PB_OK && sys->h_st[0].status == 3) {
+                // the correction of an aborted inner solve is incomplete: it
+                // is not promoted, phi keeps the last refined iterate
                 set_error("a device-side wait reached its limit in the FP32 PCG kernels");
-                return PB_ERR_TIMEOUT;
+                status = PB_ERR_TIMEOUT;
+                break;
             }
             if (rc == PB_ERR_TIMEOUT) {
                 status = PB_ERR_TIMEOUT;
@@ -1438,31 +1511,9 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
                 PB_LAUNCH_CHECK();
             }
         } else {
-            CoefS64 cp = make_s64(sys);
-            dim3 grid = stencil_grid<double>(sys->pad, KC);
-            KArgs<double> a{};
-            a.code = sys->code;
-            a.st = sys->st;
-            a.partials = sys->partials;
-            a.pg = sys->pad;
-            a.KC = KC;
-            double *pbuf[2] = {sys->pa64, sys->pb64};
-            if (which == 0 || which == 2) {
-                a.in = sys->z64;
-                a.in2 = pbuf[cur];
-                a.out = pbuf[cur ^ 1];
-                k_stencil<double, CoefS64, MODE_P, TYC, MinB<double>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
-                PB_LAUNCH_CHECK();
-            }
-            if (which == 1 || which == 2) {
-                a.in = pbuf[cur ^ 1];
-                a.in2 = nullptr;
-                a.out = nullptr;
-                a.xv = sys->x64;
-                a.zv = sys->z64;
-                k_stencil<double, CoefS64, MODE_U, TYC, MinB<double>::v><<<grid, 32 * TYC, 0, s>>>(a, cp);
-                PB_LAUNCH_CHECK();
-            }
+            launch_iter_cg64(sys, cur, KC, s, which);
+            note_launch(which == 2 ? 1 : 0);
+            PB_LAUNCH_CHECK();
         }
     }
     // phi is untouched: only the solver workspace (z, p, x increment) changed
@@ -1751,8 +1802,11 @@ pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, 
             for (int i : act) {
                 pb_system *sys = systems[i];
                 const GridGeo &g = sys->g->geo;
-                k_promote<float><<<cdiv(g.N, 256), 256, 0, s>>>(sys->phi, sys->d32, g, sys->pad);
-                note_launch(1);
+                // an aborted inner solve's correction is incomplete: not promoted
+                if (dev_status[i] != 3) {
+                    k_promote<float><<<cdiv(g.N, 256), 256, 0, s>>>(sys->phi, sys->d32, g, sys->pad);
+                    note_launch(1);
+                }
                 if ((rc = residual(sys, true, s)) != PB_OK) break;
             }
             if (rc != PB_OK) break;
@@ -1762,7 +1816,10 @@ pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, 
                 break;
             }
             for (int i : act) {
-                if (dev_status[i] == 3) status[i] = PB_ERR_TIMEOUT;
+                if (dev_status[i] == 3) {
+                    set_error("a device-side wait reached its limit in the FP32 PCG kernels");
+                    status[i] = PB_ERR_TIMEOUT;
+                }
                 iters[i] += inner_it[i];
                 const double prev = res2[i];
                 res2[i] = hst[i].res64;

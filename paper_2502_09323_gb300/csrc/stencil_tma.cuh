@@ -32,9 +32,10 @@
 // (programmatic dependent launch): every read of data that kernel wrote
 // comes after griddepcontrol.wait.
 //
-// Every wait is bounded: after TMA_WAIT_LIMIT polls a wait gives up, the
-// block records status 3 in the solver state, stops, waits (bounded) for its
-// own copies still in flight, and returns.
+// Every wait is bounded: after g_slot_wait_limit polls (TMA_WAIT_LIMIT unless
+// pb_set_wait_limit changed it) a slot wait gives up, the block records
+// status 3 in the solver state, stops, waits (bounded by TMA_WAIT_LIMIT) for
+// its own copies still in flight, and returns.
 // Included inside solve.cu's anonymous namespace (needs KArgs, CoefC32,
 // CgState and last_block_total from there).
 #pragma once
@@ -49,6 +50,9 @@ constexpr int CODEW = 160;           // code box width (bytes), x from i0-16
 constexpr int BOXH = ROWS + 2;       // rows j0-1 .. j0+ROWS
 constexpr int NTHREADS = 32 * (ROWS + 1);
 constexpr long long TMA_WAIT_LIMIT = 1ll << 20;
+// polls before a ring-slot wait (full or empty) gives up; the drain of the
+// block's own copies at exit always uses TMA_WAIT_LIMIT
+__device__ long long g_slot_wait_limit = TMA_WAIT_LIMIT;
 
 constexpr int align128(int b) { return (b + 127) & ~127; }
 constexpr int BOX_BYTES = BOXW * BOXH * 4;    // 5440
@@ -135,9 +139,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false when the limit was reached
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long n = 0; n < TMA_WAIT_LIMIT; ++n)
+// bounded wait; false when the limit was reached (at once for limit 0)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    for (long long n = 0; n < limit; ++n)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
@@ -200,7 +204,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
     using namespace tma;
     using L = SlotLayout<MODE>;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_abort, s_nsys, s_total;
+    __shared__ int s_abort, s_nsys, s_total, s_skip;
     __shared__ int s_desc[NSLOT][7];  // i0, j0, kfirst, len, system, local item, parity
     // per-descriptor warp partials of the dot products, combined without a
     // barrier: the warp that completes a descriptor's count sums them
@@ -227,13 +231,15 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
     // as SMs free up; it waits the same way before touching our results.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const long long lim = g_slot_wait_limit;
     // A one-system launch issued after its solve finished (the host polls
-    // with launches in flight) does nothing: every block leaves before
-    // touching the work counters, which the last launch left at zero.  The
-    // done flag changes only between launches, so all blocks agree.
-    if constexpr (SINGLE)
-        if (MODE != MODE_A && *(volatile int *)&e0.st->done) return;
+    // with launches in flight) takes no work: the block skips to the exit
+    // accounting below, so the last block still resets the work counters.
+    // The flag is read once per block: a block of this launch whose wait
+    // gives up sets it, so blocks that start later may see it set while
+    // earlier ones took items; every block is still counted at the exit.
     if (threadIdx.x == 0) {
+        s_skip = SINGLE && MODE != MODE_A && *(volatile int *)&e0.st->done;
         s_nsys = nsys < 0 ? (int)((volatile unsigned int *)queue)[2] : nsys;
         s_total = nsys < 0 ? (int)((volatile unsigned int *)queue)[3] : total_items;
     }
@@ -241,7 +247,9 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
     nsys = s_nsys;
     total_items = s_total;
 
-    if (w == ROWS) {
+    if (s_skip) {
+        // no work: straight to the exit accounting
+    } else if (w == ROWS) {
         // ------------------------------------------------------- producer
         if (lane == 0) {
             int last_use[NSLOT];
@@ -291,7 +299,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 bool stop = false;
                 for (int t = 0; t < nplanes; ++t, ++gt) {
                     const int s = gt % NSLOT, u = gt / NSLOT;
-                    if (u > 0 && !mbar_wait(empty0 + 8 * s, (u - 1) & 1)) {
+                    if (u > 0 && !mbar_wait(empty0 + 8 * s, (u - 1) & 1, lim)) {
                         s_abort = 1;
                         stop = true;
                         break;
@@ -333,14 +341,14 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             }
             // drain: every armed slot's copies must land before the block exits
             for (int s = 0; s < NSLOT; ++s)
-                if (last_use[s] >= 0) mbar_wait(full0 + 8 * s, last_use[s] & 1);
+                if (last_use[s] >= 0) mbar_wait(full0 + 8 * s, last_use[s] & 1, TMA_WAIT_LIMIT);
         }
     } else {
         // ------------------------------------------------------- consumers
         const int r = w + 1;  // this row inside the halo boxes
         auto slot_ptr = [&](int t) { return smem + (t % NSLOT) * L::stride; };
         auto wait_full = [&](int t) -> bool {
-            if (!mbar_wait(full0 + 8 * (t % NSLOT), (t / NSLOT) & 1)) {
+            if (!mbar_wait(full0 + 8 * (t % NSLOT), (t / NSLOT) & 1, lim)) {
                 s_abort = 1;
                 return false;
             }

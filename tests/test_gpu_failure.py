@@ -75,3 +75,42 @@ def test_engine_reports_noconv_and_keeps_serving(pb):
         assert eng.query()["rc"] == 0
     st = pb.pb_solve(a, pb.SolveOpts(precision=pb.MIXED, rtol=1e-8))
     assert st["status"] == 0
+
+
+def test_device_wait_limit_expires_then_solves(pb):
+    """Every ring-slot wait of the FP32 PCG kernels is bounded.  With the
+    bound set to zero polls the first wait gives up at once: the kernels stop,
+    drain their own copies, reset their work counters and mark the solve with
+    device status 3, which the host reports as PB_ERR_TIMEOUT -- for a single
+    solve, a batch and a served system.  With the bound restored the same
+    systems solve to the same bits as before."""
+    import time
+    opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-8)
+    a, b = _system(pb, 65), _system(pb, 81)
+    for s in (a, b):  # fixed tuning: no timing runs under the short bound
+        pb.pb_set_tuning(s, pb.MIXED, 1, 8)
+    ref = [pb.pb_solve(s, opts) for s in (a, b)]
+    phi_ref = [pb.pb_get_phi(s) for s in (a, b)]
+    try:
+        pb.pb_set_wait_limit(0)
+        st = pb.pb_solve(a, opts, check=False)
+        assert st["rc"] == -5 and st["status"] == -5, st
+        assert "device-side wait" in pb.pb_last_error()
+        sts = pb.pb_solve_batch([a, b], opts, check=False)
+        assert all(s["status"] == -5 for s in sts), sts
+        with pb.Engine(capacity=2, opts=opts) as eng:
+            eng.submit(b)
+            got, t_end = [], time.time() + 60
+            while not got and time.time() < t_end:
+                got = eng.wait(timeout_s=0.05)
+            assert len(got) == 1 and got[0]["stats"]["status"] == -5, got
+    finally:
+        pb.pb_set_wait_limit(-1)
+    for s, r, p in zip((a, b), ref, phi_ref):
+        st = pb.pb_solve(s, opts)
+        assert st["status"] == 0 and st["true_rel_res"] <= 1e-8
+        assert st["iters_inner"] == r["iters_inner"]
+        assert np.array_equal(pb.pb_get_phi(s), p)
+    sts = pb.pb_solve_batch([a, b], opts)
+    for s, p in zip((a, b), phi_ref):
+        assert np.array_equal(pb.pb_get_phi(s), p)

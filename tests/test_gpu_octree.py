@@ -39,6 +39,13 @@ CASES = {
     "mol": (lambda: pb_inputs.globular_molecule(30, seed=31),
             dict(h_fine=0.5, h_bulk=1.0, refine_dist=2.0, fill=2.0),
             dict(bc=2)),
+    # the workload's levels (0.25 / 0.5 / 1 A, refined within 3 A) on 250
+    # atoms: 3,114 bricks and 1.5M unknowns, so the persistent brick kernels
+    # run many blocks, split the transition rows over many blocks and drain
+    # a work-queue tail
+    "mid250": (lambda: pb_inputs.globular_molecule(250, seed=77),
+               dict(h_fine=0.25, h_bulk=1.0, refine_dist=3.0, fill=1.5),
+               dict(bc=2)),
 }
 
 
