@@ -70,6 +70,12 @@ def lib():
                                      P, P, C.c_long, C.c_double, C.c_double, C.c_double, P]
             L.orc_node_coeffs.argtypes = [P, P, C.c_double, P, C.c_long, C.c_double,
                                           C.c_double, C.c_double, P, C.c_long, P]
+            L.orc_mc_weights.argtypes = [P, P, C.c_long, P, P, P]
+            L.orc_mc_normals.argtypes = [C.c_long, P, P, P, C.c_long, P]
+            L.orc_coulomb_psi_n.argtypes = [P, P, C.c_long, P, C.c_long, P]
+            L.orc_energy_ion_mc.argtypes = [P, C.c_long, P, P, P, P, P, P, P, P, C.c_long,
+                                            C.c_double, C.c_double]
+            L.orc_energy_ion_mc.restype = C.c_double
             _lib = L
     return _lib
 
@@ -246,6 +252,45 @@ def energy(g: Grid, inside, cross, coef, phi, atoms, lB, eps_in, eps_out) -> dic
     return dict(zip(ENERGY_KEYS, out.tolist()))
 
 
+def mc_weights(g: Grid, inside, cross) -> np.ndarray:
+    """Vertex weights (sum of T_j/3 over the marching-cubes triangles at each
+    crossing point) of the re-triangulated surface (Sec. 3.3.2)."""
+    out = np.empty(len(cross["ids"]))
+    lib().orc_mc_weights(_p(g.n), _p(np.ascontiguousarray(inside, dtype=np.uint8)),
+                         len(cross["ids"]), _p(cross["ids"]),
+                         _p(np.ascontiguousarray(cross["rp"])), _p(out))
+    return out
+
+
+def mc_normals(cross, atoms) -> np.ndarray:
+    """Analytic outward unit normal of the ball surface at each crossing
+    point (zero where the edge's ends lie in the same medium)."""
+    atoms = _f64(atoms)
+    out = np.empty((len(cross["ids"]), 3))
+    lib().orc_mc_normals(len(cross["ids"]), _p(np.ascontiguousarray(cross["rp"])),
+                         _p(cross["sign"]), _p(atoms), len(atoms), _p(out))
+    return out
+
+
+def coulomb_psi_n(targets, normals, atoms) -> np.ndarray:
+    t = _f64(targets).reshape(-1, 3)
+    nv = _f64(normals).reshape(-1, 3)
+    atoms = _f64(atoms)
+    out = np.empty(len(t))
+    lib().orc_coulomb_psi_n(_p(t), _p(nv), len(t), _p(atoms), len(atoms), _p(out))
+    return out
+
+
+def energy_ion_mc(g: Grid, cross, W, normals, phi, atoms, eps_in, eps_out) -> float:
+    """First integral of Eq. energy_ion on the re-triangulated surface (kT)."""
+    atoms = _f64(atoms)
+    return lib().orc_energy_ion_mc(_p(g.n), len(cross["ids"]), _p(cross["ids"]),
+                                   _p(cross["alpha"]), _p(np.ascontiguousarray(cross["rp"])),
+                                   _p(cross["sign"]), _p(_f64(W)), _p(_f64(normals)),
+                                   _p(_f64(phi)), _p(atoms), len(atoms), float(eps_in),
+                                   float(eps_out))
+
+
 def node_coeffs(g: Grid, atoms, eps_in, eps_out, kD, nodes) -> np.ndarray:
     """(count, 8): W(-x), W(+x), W(-y), W(+y), W(-z), W(+z), kappa h^3, diag."""
     atoms = _f64(atoms)
@@ -274,4 +319,9 @@ def solve_problem(atoms, grid: Grid, eps_in=2.0, eps_out=80.0, ionic_strength_M=
            "relres": rel, "converged": conv}
     if with_energy:
         res["energy"] = energy(grid, inside, cross, coef, phi, atoms, lB, eps_in, eps_out)
+        W = mc_weights(grid, inside, cross)
+        nrm = mc_normals(cross, atoms)
+        res["mc"] = {"W": W, "normals": nrm}
+        res["energy"]["e_ion_mc"] = energy_ion_mc(grid, cross, W, nrm, phi, atoms, eps_in,
+                                                  eps_out)
     return res

@@ -33,7 +33,12 @@
  *
  * Parity unpinned: e_ion_surf (staircase quadrature of the first integral of
  * Eq. energy_ion) has no closed form at finite h; it is pinned only by the
- * convergence of the Kirkwood ionic energy towards its closed form.
+ * convergence of the Kirkwood ionic energy towards its closed form.  The
+ * paper's own quadrature of that integral (Sec. 3.3.2: marching cubes through
+ * the analytic intersections, vertex rule T_j/3, orc_mc_weights and
+ * orc_energy_ion_mc) is pinned by the second-order convergence of the
+ * triangulated sphere's area, the exact area of a plane, the solid angle of a
+ * union of balls and the Kirkwood ionic energy under refinement.
  */
 #include <math.h>
 #include <stdint.h>
@@ -748,4 +753,240 @@ void orc_node_coeffs(const int n[3], const double o[3], double h,
         o8[6] = kap;
         o8[7] = sum + kap;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* First integral of Eq. energy_ion (Sec. 3.3.2) on a re-triangulated       */
+/* surface.  The surface is re-triangulated cell by cell by marching cubes  */
+/* whose vertices are the analytic intersection points r_p of the crossing  */
+/* edges (edges whose end nodes differ in medium), with analytic normals;    */
+/* the integral takes the vertex rule T_j/3 on every triangle and phi at the */
+/* vertices from Eq. phi0.                                                   */
+/*                                                                          */
+/* Triangulation of one cell, without a case table: on each of the six      */
+/* faces the crossing edges are joined in pairs (two crossings: one         */
+/* segment; four, the ambiguous face, two segments that each cut off one    */
+/* inside corner, so the two cells sharing a face agree and the surface is  */
+/* closed).  Every crossing edge of the cell lies on two faces, so the      */
+/* segments form closed loops.  Each loop starts at its lowest cell-edge    */
+/* index, goes first to the smaller of that vertex's two neighbours, and is */
+/* cut into the fan of triangles (v0, v_m, v_m+1).                           */
+/* ------------------------------------------------------------------------ */
+
+/* cell corners: bit 0 = +x, bit 1 = +y, bit 2 = +z.  Cell edges 0..11:
+ * along x (0,1) (2,3) (4,5) (6,7); along y (0,2) (1,3) (4,6) (5,7);
+ * along z (0,4) (1,5) (2,6) (3,7). */
+static const int mc_edge_corner[12][2] = {
+    {0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7},
+    {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+/* faces as four corners in cyclic order */
+static const int mc_face[6][4] = {
+    {0, 2, 6, 4}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 5, 7, 6}};
+
+static int mc_edge_of(int ca, int cb)
+{
+    for (int e = 0; e < 12; ++e)
+        if ((mc_edge_corner[e][0] == ca && mc_edge_corner[e][1] == cb) ||
+            (mc_edge_corner[e][0] == cb && mc_edge_corner[e][1] == ca))
+            return e;
+    return -1;
+}
+
+/* index of edge id in the sorted crossing list, -1 if absent */
+static long find_edge(const int64_t *ids, long ncross, int64_t id)
+{
+    long lo = 0, hi = ncross - 1;
+    while (lo <= hi) {
+        long mid = lo + (hi - lo) / 2;
+        if (ids[mid] == id) return mid;
+        if (ids[mid] < id) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* Triangles of cell (i,j,k): writes up to 12 triangles as triples of
+ * crossing-list indices into tri (fan order) and their areas; returns the
+ * triangle count. */
+static int mc_cell(const int *n, const uint8_t *inside, long ncross, const int64_t *ids,
+                   const double *rp, long i, long j, long k, long *tri, double *area)
+{
+    long N = (long)n[0] * n[1] * n[2];
+    long node[8];
+    int ins[8];
+    int any_in = 0, any_out = 0;
+    for (int c = 0; c < 8; ++c) {
+        long a = ((k + ((c >> 2) & 1)) * n[1] + (j + ((c >> 1) & 1))) * n[0] + (i + (c & 1));
+        node[c] = a;
+        ins[c] = inside[a] ? 1 : 0;
+        if (ins[c]) any_in = 1;
+        else any_out = 1;
+    }
+    if (!(any_in && any_out)) return 0;
+    long vert[12];
+    for (int e = 0; e < 12; ++e) {
+        int ca = mc_edge_corner[e][0], cb = mc_edge_corner[e][1];
+        vert[e] = -1;
+        if (ins[ca] != ins[cb]) {
+            int d = e / 4;
+            vert[e] = find_edge(ids, ncross, (int64_t)d * N + node[ca]);
+        }
+    }
+    int nbr[12][2], deg[12];
+    for (int e = 0; e < 12; ++e) deg[e] = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int *c = mc_face[f];
+        int fe[4];
+        for (int q = 0; q < 4; ++q) fe[q] = mc_edge_of(c[q], c[(q + 1) & 3]);
+        int cr[4], m = 0;
+        for (int q = 0; q < 4; ++q)
+            if (ins[c[q]] != ins[c[(q + 1) & 3]]) cr[m++] = q;
+        int pairs[2][2], np = 0;
+        if (m == 2) {
+            pairs[0][0] = fe[cr[0]];
+            pairs[0][1] = fe[cr[1]];
+            np = 1;
+        } else if (m == 4) {
+            /* cut off each inside corner: corner q lies between face edges
+             * q-1 and q */
+            int q0 = ins[c[0]] ? 0 : 1;
+            pairs[0][0] = fe[(q0 + 3) & 3];
+            pairs[0][1] = fe[q0];
+            pairs[1][0] = fe[(q0 + 1) & 3];
+            pairs[1][1] = fe[(q0 + 2) & 3];
+            np = 2;
+        }
+        for (int p = 0; p < np; ++p) {
+            int a = pairs[p][0], b = pairs[p][1];
+            nbr[a][deg[a]++] = b;
+            nbr[b][deg[b]++] = a;
+        }
+    }
+    int seen[12] = {0};
+    int nt = 0;
+    for (int e0 = 0; e0 < 12; ++e0) {
+        if (ins[mc_edge_corner[e0][0]] == ins[mc_edge_corner[e0][1]] || seen[e0]) continue;
+        int loop[12], len = 0;
+        int prev = e0;
+        int cur = nbr[e0][0] < nbr[e0][1] ? nbr[e0][0] : nbr[e0][1];
+        loop[len++] = e0;
+        seen[e0] = 1;
+        while (cur != e0 && len < 12) {
+            loop[len++] = cur;
+            seen[cur] = 1;
+            int nx = nbr[cur][0] == prev ? nbr[cur][1] : nbr[cur][0];
+            prev = cur;
+            cur = nx;
+        }
+        for (int m = 1; m + 1 < len; ++m) {
+            long a = vert[loop[0]], b = vert[loop[m]], c = vert[loop[m + 1]];
+            if (a < 0 || b < 0 || c < 0) continue;
+            const double *pa = rp + 3 * a, *pb = rp + 3 * b, *pc = rp + 3 * c;
+            double u[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+            double v[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
+            double x = u[1] * v[2] - u[2] * v[1];
+            double y = u[2] * v[0] - u[0] * v[2];
+            double z = u[0] * v[1] - u[1] * v[0];
+            tri[3 * nt] = a;
+            tri[3 * nt + 1] = b;
+            tri[3 * nt + 2] = c;
+            area[nt] = 0.5 * sqrt((x * x + y * y) + z * z);
+            ++nt;
+        }
+    }
+    return nt;
+}
+
+/* Vertex weights of the re-triangulated surface: W[s] = sum of T_j / 3 over
+ * the triangles that have crossing point s as a vertex (0 for edges whose
+ * end nodes lie in the same medium).  Cells are visited in node order. */
+void orc_mc_weights(const int n[3], const uint8_t *inside, long ncross, const int64_t *ids,
+                    const double *rp, double *W)
+{
+    long tri[36];
+    double area[12];
+    for (long s = 0; s < ncross; ++s) W[s] = 0.0;
+    for (long k = 0; k + 1 < n[2]; ++k)
+        for (long j = 0; j + 1 < n[1]; ++j)
+            for (long i = 0; i + 1 < n[0]; ++i) {
+                int nt = mc_cell(n, inside, ncross, ids, rp, i, j, k, tri, area);
+                for (int t = 0; t < nt; ++t)
+                    for (int v = 0; v < 3; ++v) W[tri[3 * t + v]] += area[t] / 3.0;
+            }
+}
+
+/* Analytic outward normal of the union of balls at each crossing point with
+ * sign != 0: the unit vector from the centre of the ball whose sphere passes
+ * closest to the point (smallest | |r_p - c_i| - R_i |, ties to the lower
+ * atom index).  Zero for the other edges. */
+void orc_mc_normals(long ncross, const double *rp, const int8_t *sign, const double *atoms,
+                    long na, double *nrm)
+{
+    for (long s = 0; s < ncross; ++s) {
+        double *o = nrm + 3 * s;
+        o[0] = o[1] = o[2] = 0.0;
+        if (sign[s] == 0) continue;
+        const double *p = rp + 3 * s;
+        long best = -1;
+        double bdev = 0.0, bd = 0.0;
+        for (long a = 0; a < na; ++a) {
+            const double *c = atoms + 5 * a;
+            double dx = p[0] - c[0], dy = p[1] - c[1], dz = p[2] - c[2];
+            double d = sqrt((dx * dx + dy * dy) + dz * dz);
+            double dev = fabs(d - c[3]);
+            if (best < 0 || dev < bdev) {
+                best = a;
+                bdev = dev;
+                bd = d;
+            }
+        }
+        const double *c = atoms + 5 * best;
+        o[0] = (p[0] - c[0]) / bd;
+        o[1] = (p[1] - c[1]) / bd;
+        o[2] = (p[2] - c[2]) / bd;
+    }
+}
+
+/* Psi with a general normal: sum_i q_i (r_t - r_i).n_t / |r_t - r_i|^3 */
+void orc_coulomb_psi_n(const double *tgt, const double *nrm, long nt, const double *atoms,
+                       long na, double *out)
+{
+    for (long t = 0; t < nt; ++t) {
+        const double *p = tgt + 3 * t, *nv = nrm + 3 * t;
+        double acc = 0.0;
+        for (long a = 0; a < na; ++a) {
+            const double *c = atoms + 5 * a;
+            double dx = p[0] - c[0], dy = p[1] - c[1], dz = p[2] - c[2];
+            double r2 = (dx * dx + dy * dy) + dz * dz;
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            acc += c[4] * ((dx * nv[0] + dy * nv[1]) + dz * nv[2]) / (r2 * r);
+        }
+        out[t] = acc;
+    }
+}
+
+/* E_ion first integral on the re-triangulated surface:
+ * 1/2 sum_s W_s phi(r_s) Psi_n(r_s) / (4 pi), phi(r_s) by Eq. phi0 from the
+ * edge's two end nodes (alpha = inside fraction from the inside node). */
+double orc_energy_ion_mc(const int n[3], long ncross, const int64_t *ids, const double *alpha,
+                         const double *rp, const int8_t *sign, const double *W,
+                         const double *nrm, const double *phi, const double *atoms, long na,
+                         double eps_in, double eps_out)
+{
+    double I = 0.0;
+    for (long s = 0; s < ncross; ++s) {
+        if (sign[s] == 0 || W[s] == 0.0) continue;
+        int d;
+        long a, b;
+        edge_nodes(n, ids[s], &d, &a, &b);
+        long in = sign[s] > 0 ? a : b, out_n = sign[s] > 0 ? b : a;
+        double al = alpha[s];
+        double pin = phi[in], pout = phi[out_n];
+        double phip = pin + (al / eps_in) * (pout - pin) / (al / eps_in + (1.0 - al) / eps_out);
+        double psi;
+        orc_coulomb_psi_n(rp + 3 * s, nrm + 3 * s, 1, atoms, na, &psi);
+        I += W[s] * phip * psi;
+    }
+    return 0.5 * I / (4.0 * M_PI);
 }

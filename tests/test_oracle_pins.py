@@ -435,3 +435,107 @@ def test_gauss_identity_molecule(orc):
     r = orc.solve_problem(atoms, g, rtol=1e-12)
     Q = atoms[:, 4].sum()
     assert abs(r["energy"]["flux_charge"] - Q) < 1e-8 * max(1.0, np.abs(atoms[:, 4]).sum())
+
+
+# --------------------------------------------------------------------------
+# first integral of Eq. energy_ion on the re-triangulated surface (Sec. 3.3.2)
+# --------------------------------------------------------------------------
+
+def _sphere_mc(orc, n, L, c, R):
+    h = L / (n - 1)
+    atoms = np.array([[*c, R, 1.0]])
+    g = orc.Grid((n, n, n), (0.0, 0.0, 0.0), h)
+    ins = orc.classify(g, atoms)
+    cr = orc.crossing_edges(g, atoms, ins)
+    return atoms, g, cr, orc.mc_weights(g, ins, cr), orc.mc_normals(cr, atoms)
+
+
+def test_mc_surface_area_converges_second_order(orc):
+    """The marching-cubes triangles through the exact intersection points
+    approximate a sphere: their total area tends to 4 pi R^2 with an error
+    that falls fourfold when h halves (the staircase faces never converge)."""
+    R, L = 2.0, 8.0
+    c = (L / 2 + 0.0123, L / 2 - 0.0311, L / 2 + 0.0207)
+    errs = []
+    for n in (17, 33, 65):
+        _, _, cr, W, _ = _sphere_mc(orc, n, L, c, R)
+        assert np.all(W[cr["sign"] == 0] == 0.0) and np.all(W[cr["sign"] != 0] > 0.0)
+        errs.append(abs(W.sum() / (4 * math.pi * R * R) - 1.0))
+    assert errs[0] < 2e-2 and errs[2] < 1.2e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_mc_surface_of_a_plane_is_exact(orc):
+    """A ball of radius 1e6 is a plane on the scale of the grid: inside every
+    cell the marching-cubes polygon is the plane's cross-section, so the
+    total area is that of the plane inside the box, L^2 |n| / |n_z| for the
+    tilted normal n = (0.2, 0.1, 1)."""
+    n, L, R = 21, 4.0, 1e6
+    nv = np.array([0.2, 0.1, 1.0])
+    nv /= np.linalg.norm(nv)
+    p0 = np.array([L / 2 + 0.013, L / 2 - 0.021, L / 2 + 0.007])
+    atoms, g, cr, W, nrm = _sphere_mc(orc, n, L, p0 - R * nv, R)
+    expect = L * L / nv[2]
+    assert abs(W.sum() / expect - 1.0) < 1e-9
+    flux = cr["sign"] != 0
+    assert np.allclose(nrm[flux], nv, atol=1e-5)
+
+
+def test_mc_normals_belong_to_the_exposed_sphere(orc):
+    """Each vertex normal is the unit vector from the centre of a ball whose
+    sphere passes through the vertex, and the vertex lies in no other ball."""
+    atoms = np.array([[4.0, 4.0, 4.0, 1.8, 1.0], [5.9, 4.3, 4.1, 1.5, -0.5],
+                      [4.2, 5.7, 3.6, 1.3, 0.25]])
+    g = orc.Grid((33, 33, 33), (0.0, 0.0, 0.0), 0.3)
+    ins = orc.classify(g, atoms)
+    cr = orc.crossing_edges(g, atoms, ins)
+    nrm = orc.mc_normals(cr, atoms)
+    flux = np.flatnonzero(cr["sign"] != 0)
+    assert np.allclose(np.linalg.norm(nrm[flux], axis=1), 1.0, atol=1e-14)
+    for s in flux:
+        p = cr["rp"][s]
+        d = np.linalg.norm(p - atoms[:, :3], axis=1)
+        owner = [a for a in range(3) if np.allclose(p - atoms[a, :3], nrm[s] * d[a], atol=1e-12)]
+        assert owner and abs(d[owner[0]] - atoms[owner[0], 3]) < 1e-9
+        assert np.all(d >= atoms[:, 3] - 1e-9)
+
+
+def test_mc_solid_angle_of_a_union_of_balls(orc):
+    """Gauss: the solid angle of a closed surface seen from a point inside is
+    4 pi.  The vertex rule on the re-triangulated union of three balls gives
+    it to within about 1e-2, closing in under refinement (the creases where
+    spheres meet keep the rate near first order)."""
+    atoms = np.array([[4.0, 4.0, 4.0, 1.8, 1.0], [5.9, 4.3, 4.1, 1.5, -0.5],
+                      [4.2, 5.7, 3.6, 1.3, 0.25]])
+    x = np.array([4.6, 4.4, 4.0])
+    errs = []
+    for n, h in ((33, 0.3), (65, 0.15)):
+        g = orc.Grid((n, n, n), (0.0, 0.0, 0.0), h)
+        ins = orc.classify(g, atoms)
+        cr = orc.crossing_edges(g, atoms, ins)
+        W = orc.mc_weights(g, ins, cr)
+        nrm = orc.mc_normals(cr, atoms)
+        d = cr["rp"] - x
+        r = np.linalg.norm(d, axis=1)
+        errs.append(abs((W * np.einsum("ij,ij->i", d, nrm) / r ** 3).sum() / (4 * math.pi) - 1))
+    assert errs[0] < 3e-2 and errs[1] < 0.5 * errs[0] and errs[1] < 1e-2
+
+
+def test_kirkwood_eion_with_mc_surface_converges(orc):
+    """Kirkwood sphere in 0.145 M salt (Sec. 6.1.1): the paper's E_ion, the
+    first integral on the re-triangulated surface plus the flux term,
+    converges to the closed form, and beats the staircase quadrature at
+    every spacing."""
+    lB, kD = orc.units(298.15, 0.145, 80.0)
+    e_ion = -0.5 * lB / 80.0 * kD / (1.0 + kD * 2.0)
+    errs = []
+    for n, h in ((33, 0.5), (65, 0.25)):
+        atoms, g = _centered_sphere(orc, n, h)
+        r = orc.solve_problem(atoms, g, eps_in=2.0, eps_out=80.0, ionic_strength_M=0.145,
+                              bc=orc.BC_DH, rtol=1e-11)
+        e = r["energy"]
+        mc = abs(e["e_ion_mc"] + e["e_ion_flux"] - e_ion) / abs(e_ion)
+        stair = abs(e["e_ion_surf"] + e["e_ion_flux"] - e_ion) / abs(e_ion)
+        assert mc < stair
+        errs.append(mc)
+    assert errs[0] < 0.06 and errs[1] < 0.6 * errs[0]
