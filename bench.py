@@ -66,6 +66,17 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=None,
                     help="Poisson arrival rate (default 1.5/s on octree grids, 6/s on uniform)")
     ap.add_argument("--serve-grid", default="octree", choices=["octree", "uniform"])
+    ap.add_argument("--grid-n", type=int, default=None,
+                    help="nodes per axis of the uniform workload instead of its own (profiling "
+                         "captures of smaller cases)")
+    ap.add_argument("--profile-fp64", action="store_true",
+                    help="run only W + K plain FP64 steps of the uniform workload (profiling)")
+    ap.add_argument("--serve-sweep", default=None,
+                    help="comma-separated Poisson rates (1/s): serve --serve-requests requests at "
+                         "each rate and report every operating point (long; not in the default run)")
+    ap.add_argument("--oracle-procs", type=int, default=None,
+                    help="host processes for the oracle throughput of the batched workload "
+                         "(default: the cores this process may use)")
     ap.add_argument("--tuning", default=None,
                     help="VARIANT:ZCHUNK for the FP32 PCG kernels instead of the autotuner "
                          "(e.g. 1:0 = TMA-staged persistent); for profiler runs")
@@ -134,13 +145,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle --
-def oracle_sample(wl: dict, iters_needed: int | None, pcg_iters: int = 3,
-                  targets: int = 2000) -> dict:
+def oracle_sample(wl: dict, pcg_iters: int = 10, targets: int = 2000) -> dict:
     """Time the FP64 oracle on a bounded sample of the workload and
     extrapolate one full solve: full setup (classification, crossing edges,
-    coefficients, right-hand side) + `pcg_iters` PCG iterations scaled to
-    `iters_needed` + surface sums on `targets` flux points scaled to all of
-    them + the full pair sum."""
+    coefficients, right-hand side) + `pcg_iters` PCG iterations scaled to the
+    oracle's own iteration count to rtol (recorded by ``python -m
+    oracle.calibrate``) + surface sums on `targets` flux points scaled to all
+    of them + the full pair sum."""
     import numpy as np
 
     import pb_inputs
@@ -156,9 +167,14 @@ def oracle_sample(wl: dict, iters_needed: int | None, pcg_iters: int = 3,
     phib = orc.bc_values(g, atoms, lB, wl["eps_out"], wl["bc"], kD)
     f = orc.rhs(g, atoms, lB, coef, phib)
     t_setup = time.perf_counter() - t0
+    # iteration time from two runs of different length: the difference
+    # leaves out the first iterations' page faults and cold caches
     t0 = time.perf_counter()
-    orc.pcg(g, coef, f, wl["rtol"], max_iter=pcg_iters)
-    t_iter = (time.perf_counter() - t0) / pcg_iters
+    orc.pcg(g, coef, f, wl["rtol"], max_iter=2)
+    t_short = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.pcg(g, coef, f, wl["rtol"], max_iter=2 + pcg_iters)
+    t_iter = max(time.perf_counter() - t0 - t_short, 0.0) / pcg_iters
     flux = cross["sign"] != 0
     nflux = int(flux.sum())
     sel = np.flatnonzero(flux)[:: max(1, nflux // targets)][:targets]
@@ -170,28 +186,47 @@ def oracle_sample(wl: dict, iters_needed: int | None, pcg_iters: int = 3,
     t0 = time.perf_counter()
     orc.ecoul(atoms, lB, wl["eps_in"])
     t_pairs = time.perf_counter() - t0
-    iters = iters_needed or oracle_iters()
+    iters = oracle_iters()
     t_solve = t_setup + iters * t_iter + t_surf + t_pairs
     return {"t_setup": t_setup, "t_iter": t_iter, "iters": iters, "t_surface": t_surf,
             "t_pairs": t_pairs, "t_solve": t_solve, "nflux": nflux, "sampled_targets": len(sel),
             "pcg_iters_sampled": pcg_iters}
 
 
-def oracle_iters() -> int:
-    """FP64 Jacobi-PCG iterations of the oracle to a 1e-8 true residual on
-    the default workload, as recorded by ``python -m oracle.calibrate`` (the
-    GPU FP64 path runs the same recurrence and reports its own count)."""
+def oracle_record() -> dict:
+    """The oracle's complete run on the default workload as recorded by
+    ``python -m oracle.calibrate``: its Jacobi-PCG iteration count to a 1e-8
+    true residual and the measured seconds of the whole pass (with the
+    machine it ran on)."""
     with open(os.path.join(ROOT, "oracle", "iters_globular257.json")) as fh:
-        return int(json.load(fh)["iters"])
+        return json.load(fh)
+
+
+def oracle_iters() -> int:
+    return int(oracle_record()["iters"])
+
+
+def full_solve_check() -> dict | None:
+    """The recorded, measured full oracle pass when it was taken on a machine
+    of this architecture (the projection of the sample can be read against
+    it)."""
+    import platform
+    rec = oracle_record()
+    if rec.get("machine") != platform.machine() or "seconds_full" not in rec:
+        return None
+    return {"seconds_measured": rec["seconds_full"], "iters": rec["iters"],
+            "machine": rec["machine"], "source": "oracle/iters_globular257.json "
+            "(python -m oracle.calibrate: one complete oracle pass, grid to energy)"}
 
 
 def cpu_baseline_obj(s: dict) -> dict:
     return {"value": 1.0 / s["t_solve"], "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"full FP64 setup ({s['t_setup']:.1f} s), {s['pcg_iters_sampled']} PCG "
-                       f"iterations scaled to {s['iters']}, surface sums on "
-                       f"{s['sampled_targets']} of {s['nflux']} flux points scaled, full pair "
-                       f"sum; one host core, single-threaded C"),
-            "seconds_per_solve_est": s["t_solve"]}
+            "sample": (f"projection of one full solve from a measured sample: full FP64 setup "
+                       f"({s['t_setup']:.1f} s), {s['pcg_iters_sampled']} PCG iterations after 2 "
+                       f"({s['t_iter']:.3f} s each) scaled to the oracle's own {s['iters']}, "
+                       f"surface sums on {s['sampled_targets']} of {s['nflux']} flux points "
+                       f"scaled, full pair sum; one host core, single-threaded C"),
+            "seconds_per_solve_est": s["t_solve"], "full_solve_check": full_solve_check()}
 
 
 def run_reference(args, wl):
@@ -199,23 +234,26 @@ def run_reference(args, wl):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        oracle_sample(wl, None, pcg_iters=1, targets=200)
+        oracle_sample(wl, pcg_iters=1, targets=200)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_sample(wl, None))
+        vals.append(oracle_sample(wl))
     wall = time.perf_counter() - t0
     t_solve = statistics.mean(v["t_solve"] for v in vals)
     value = 1.0 / t_solve
+    # each step is one measured sample (ms_per_step is its wall time); the
+    # value projects one full solve from the samples
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_solve, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_obj(args, wl),
             "cpu_baseline": dict(cpu_baseline_obj(vals[-1]), value=value),
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
-            "sample_wall_s": wall}
+            "value_kind": "projected seconds per full solve from the measured per-step samples",
+            "projected_s_per_solve": t_solve, "sample_wall_s": wall}
     print(json.dumps(line))
     return 0
 
@@ -274,6 +312,36 @@ def run_batched(args, pb, pb_inputs, torch):
     torch.cuda.synchronize()
     t64 = a.elapsed_time(b) / 1e3
     e64 = [pb.pb_energy(s)["e_total"] for s in systems[:8]]
+    # the oracle's throughput on a seeded subsample of the batch: every
+    # sampled molecule is one complete oracle pass on the grid of its GPU
+    # solve, in its own host process; the GPU energies of the same molecules
+    # (mixed precision, from the batch above) are compared with the oracle's
+    cpu = None
+    if not args.no_cpu_baseline:
+        import numpy as np
+        rng = np.random.Generator(np.random.PCG64(4001))
+        pick = sorted(int(i) for i in rng.choice(count, size=min(16, count), replace=False))
+        procs = args.oracle_procs or min(host_cores(), len(pick))
+        e_gpu = {}
+        for i in pick:
+            pb.pb_solve_batch([systems[i]], mixed)
+            e_gpu[i] = pb.pb_energy(systems[i])["e_total"]
+        jobs = [(mols[i], specs[i].n[0], specs[i].origin, specs[i].h) for i in pick]
+        with oracle_pool(procs) as pool:
+            t0 = time.perf_counter()
+            res = list(pool.map(_oracle_uniform_job, jobs))
+            wall = time.perf_counter() - t0
+        secs = [r[0] for r in res]
+        cpu = {"value": len(pick) / wall, "unit": "solves/s", "cores": procs, "kind": "oracle",
+               "sample": (f"{len(pick)} of the {count} molecules (seeded choice, grids "
+                          f"{sorted({specs[i].n[0] for i in pick})}), each one complete oracle "
+                          f"pass (grid to energy, FP64 PCG to 1e-8) in its own process, {procs} "
+                          f"processes on {host_cores()} host cores; value = sampled molecules / "
+                          "wall time of the sample"),
+               "sample_wall_s": wall, "seconds_per_molecule": secs,
+               "projected_batch_s": sum(secs) / procs * count / len(pick),
+               "energy_rel_diff_gpu_vs_oracle_max": max(
+                   abs(e_gpu[i] - r[2]) / abs(r[2]) for i, r in zip(pick, res))}
     dof = [x["dof"] for x in st]
     iters = [x["iters_inner"] for x in st]
     shapes = {}
@@ -294,6 +362,7 @@ def run_batched(args, pb, pb_inputs, torch):
         "fp64_true_rel_res_max": max(x["true_rel_res"] for x in st64),
         "all_converged": all(x["status"] == 0 for x in st) and all(x["status"] == 0 for x in st64),
         "energy_rel_diff_mixed_vs_fp64_max": max(abs(m - f) / abs(f) for m, f in zip(e_mixed, e64)),
+        "cpu_baseline": cpu,
     }
     del systems
     torch.cuda.synchronize()
@@ -468,6 +537,119 @@ def run_serving(args, pb, pb_inputs, torch):
     return out
 
 
+def _oracle_uniform_job(job):
+    """One complete oracle pass (grid to energy) of one molecule on the grid
+    of its GPU solve, in a worker process; returns (seconds, iterations,
+    E_total)."""
+    atoms, n, origin, h = job
+    from oracle import oracle as orc
+    g = orc.Grid((n, n, n), origin, h)
+    t0 = time.perf_counter()
+    r = orc.solve_problem(atoms, g, rtol=1e-8, with_energy=True)
+    return time.perf_counter() - t0, int(r["iters"]), float(r["energy"]["e_total"])
+
+
+def _oracle_octree_job(job):
+    """Octree oracle pass (grid to energy) of one served molecule."""
+    atoms, h_fine, h_bulk, refine_dist, fill = job
+    from oracle import octree
+    from oracle import oracle as orc
+    orc.build()
+    t0 = time.perf_counter()
+    tree = octree.build(atoms, h_fine, h_bulk, refine_dist, fill=fill)
+    r = octree.solve_problem(atoms, tree, rtol=1e-10)
+    return time.perf_counter() - t0, float(r["energy"]["e_total"])
+
+
+def oracle_pool(procs: int):
+    """Worker processes for the oracle, started with spawn (never forked
+    from a process that holds a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle import oracle as orc
+    orc.build()
+    return cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn"))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_serve_sweep(args):
+    """The serving workload at several Poisson rates (``inf``: every request
+    arrives at once, the engine's saturation throughput); per rate the
+    latency percentiles, throughput and budget used.  The two smallest
+    requests are also solved by the octree oracle (FP64, rtol 1e-10) in host
+    processes while the GPU serves, and their served energies are compared
+    with it."""
+    import torch
+
+    import paper_2502_09323_gb300 as pb
+    import pb_inputs
+    from paper_2502_09323_gb300 import build, serving
+    count = args.serve_requests
+    rates = [float(r) for r in args.serve_sweep.split(",")]
+    sizes = pb_inputs.batch_sizes(count, 5000, 300, 50000)
+    mols = [pb_inputs.globular_molecule(int(n), seed=5000 + j) for j, n in enumerate(sizes)]
+    small = sorted(range(count), key=lambda j: len(mols[j]))[:2]
+    pool = oracle_pool(2)
+    futs = {j: pool.submit(_oracle_octree_job, (mols[j], 0.25, 1.0, 3.0, 1.5)) for j in small}
+    build.build()
+    torch.cuda.set_device(0)
+    opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-8)
+    with pb.Engine(capacity=4, opts=opts) as eng:  # warm-up
+        one = pb_inputs.globular_molecule(300, seed=4999)
+        g = pb.pb_build_grid(serving.octree_spec(one), one)
+        s = pb.pb_assemble_coeffs(g, pb.Params())
+        eng.submit(s)
+        while not eng.wait(timeout_s=0.1):
+            pass
+        del s, g
+    points = []
+    served_e = {}
+    for rate in rates:
+        if math.isinf(rate):
+            arrivals = [0.0] * count
+        else:
+            arrivals = pb_inputs.poisson_arrivals(count, rate, seed=5000)
+        reqs = [serving.Request(rid=j, atoms=mols[j], arrival_s=float(t))
+                for j, t in enumerate(arrivals)]
+        with serving.Server(capacity=64, hbm_budget_bytes=150e9, opts=opts, h=0.25,
+                            grid="octree") as srv:
+            recs = srv.run(reqs)
+            max_used = srv.max_used
+        for r in recs:
+            if r["rid"] in small and r["rid"] not in served_e:
+                served_e[r["rid"]] = r["energy"]["e_total"]
+        summ = serving.latency_summary(recs)
+        points.append({"rate_hz": rate if not math.isinf(rate) else "all at once", **summ,
+                       "max_budget_used_gb": max_used / 1e9,
+                       "all_converged": all(r["stats"]["status"] == 0 for r in recs),
+                       "true_rel_res_max": max(r["stats"]["true_rel_res"] for r in recs)})
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    oracle = []
+    for j in small:
+        secs, e_orc = futs[j].result()
+        oracle.append({"rid": j, "atoms": len(mols[j]), "e_total_served": served_e[j],
+                       "e_total_oracle": e_orc, "rel_diff": abs(served_e[j] - e_orc) / abs(e_orc),
+                       "oracle_seconds": secs})
+    pool.shutdown()
+    offered = [p["rate_hz"] for p in points]
+    print(json.dumps({"serving_sweep": {
+        "workload": f"{count} requests per rate, Poisson arrivals (seed 5000), globular molecules "
+                    "with atoms log-uniform [300, 50000] (molecule j seeded 5000 + j), brick "
+                    "octrees h 0.25..1 A refined within 3 A of the atom spheres, fill 1.5, mixed "
+                    "precision to 1e-8, 150 GB budget, 64 slots",
+        "rates_offered": offered, "points": points,
+        "saturation_solves_per_s": max(p["solves_per_s"] for p in points),
+        "energy_vs_octree_oracle": oracle}}))
+    return 0
+
+
 # ------------------------------------------------------------- ranks --
 def max_over_ranks_of(v: float, dist, device) -> float:
     """Largest value over all ranks (the slowest rank's time); v itself
@@ -633,8 +815,7 @@ def run_ours(args, wl):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        smp = oracle_sample(wl, fp64["iters"] if fp64 else None)
-        cpu = cpu_baseline_obj(smp)
+        cpu = cpu_baseline_obj(oracle_sample(wl))
 
     octree = None if args.no_octree else run_octree(args, pb, pb_inputs, torch)
     batched = None if args.no_batched else run_batched(args, pb, pb_inputs, torch)
@@ -671,11 +852,44 @@ def run_ours(args, wl):
     return 0
 
 
+def run_profile_fp64(args, wl):
+    """W + K whole-path steps with the plain FP64 solver only (for profiler
+    captures of its kernels); prints the solve statistics."""
+    import torch
+
+    import paper_2502_09323_gb300 as pb
+    import pb_inputs
+    from paper_2502_09323_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    atoms = torch.tensor(pb_inputs.globular_molecule(wl["n_atoms"], seed=wl["seed"]), device="cuda")
+    spec = pb.GridSpec(n=(wl["n"],) * 3, fill=wl["fill"])
+    params = pb.Params(eps_in=wl["eps_in"], eps_out=wl["eps_out"], ionic_strength_M=wl["ionic"],
+                       bc=wl["bc"])
+    out = []
+    for i in range(args.warmup + args.steps):
+        g = pb.pb_build_grid(spec, atoms)
+        s = pb.pb_assemble_coeffs(g, params)
+        st = pb.pb_solve(s, pb.SolveOpts(precision=pb.FP64, rtol=wl["rtol"]))
+        if i >= args.warmup:
+            out.append({k: st[k] for k in ("iters_inner", "true_rel_res", "seconds", "dof")})
+        del s, g
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_fp64": out, "grid": wl["n"]}))
+    return 0
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
+    if args.grid_n:
+        wl = dict(wl, n=args.grid_n)
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.profile_fp64:
+        return run_profile_fp64(args, wl)
+    if args.serve_sweep:
+        return run_serve_sweep(args)
     if args.octree_only:
         import torch
 

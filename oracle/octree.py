@@ -40,6 +40,15 @@ following reading, which the GPU library implements independently:
   that every solute node, every edge meeting the surface and every charge
   cell lies in the all-finest region (where everything matches the uniform
   grid at h_fine), and every row next to a level change sees solvent only.
+* De-refined domain (Sec. 3.4, "Exploiting de-refinement for more efficient
+  BCs"): with h_tight set, h_bulk is the spacing of the coarse far field and
+  a level-l brick is also split while its cells are coarser than h_tight and
+  its closed box meets the tight box: a cube of side tight_fill * extent
+  centred on the same bounding box (tight_fill about 1.1, a perfil near
+  90 %).  The domain itself (fill) can then be several times the extent (a
+  perfil of 15-20 %), where null Dirichlet values are accurate.  The
+  refine_dist condition uses h_tight in place of h_bulk: cells coarser than
+  h_tight lie outside the tight box, away from the molecule.
 """
 from __future__ import annotations
 
@@ -142,15 +151,33 @@ def _box_max(field: np.ndarray, f: int) -> np.ndarray:
     return field.reshape(n, f, n, f, n, f).max(axis=(1, 3, 5))
 
 
+def tight_box(atoms: np.ndarray, tight_fill: float):
+    """Low and high corners of the tight box: a cube of side tight_fill *
+    extent centred on the bounding box of the atom spheres."""
+    lo = (atoms[:, :3] - atoms[:, 3:4]).min(axis=0)
+    hi = (atoms[:, :3] + atoms[:, 3:4]).max(axis=0)
+    half = 0.5 * tight_fill * float((hi - lo).max())
+    c = 0.5 * (lo + hi)
+    return c - half, c + half
+
+
 def build(atoms, h_fine: float, h_bulk: float, refine_dist: float, fill: float = 1.5,
-          origin=None, n0: int | None = None) -> Octree:
+          origin=None, n0: int | None = None, h_tight: float | None = None,
+          tight_fill: float = 1.1) -> Octree:
     atoms = np.ascontiguousarray(atoms, dtype=np.float64)
     ratio = h_bulk / h_fine
     Lmax = int(round(math.log2(ratio)))
     if Lmax < 0 or h_fine * (1 << Lmax) != h_bulk:
         raise ValueError("h_bulk must be h_fine times a power of two")
-    if refine_dist < max(float(atoms[:, 3].max()), h_fine, 1.5 * h_bulk):
-        raise ValueError("refine_dist must be at least the largest radius, h_fine and 1.5 h_bulk")
+    h_near = h_bulk
+    if h_tight is not None:
+        Lt = int(round(math.log2(h_bulk / h_tight)))
+        if Lt < 0 or Lt > Lmax or h_tight * (1 << Lt) != h_bulk:
+            raise ValueError("h_tight must be h_bulk over a power of two, at least h_fine")
+        h_near = h_tight
+    if refine_dist < max(float(atoms[:, 3].max()), h_fine, 1.5 * h_near):
+        raise ValueError("refine_dist must be at least the largest radius, h_fine and 1.5 h_bulk "
+                         "(h_tight on a de-refined domain)")
     if origin is None:
         origin, n0 = place(atoms, h_bulk, fill)
     origin = np.asarray(origin, dtype=np.float64)
@@ -162,7 +189,14 @@ def build(atoms, h_fine: float, h_bulk: float, refine_dist: float, fill: float =
         nl = n0 << l
         g = np.stack(np.meshgrid(np.arange(nl), np.arange(nl), np.arange(nl), indexing="ij"), -1)
         low = g.reshape(-1, 3) * (8 * f)
-        near = near_boxes(atoms, origin, h_fine, low, 8 * f, refine_dist).reshape(nl, nl, nl)
+        near = near_boxes(atoms, origin, h_fine, low, 8 * f, refine_dist)
+        if h_tight is not None and l < Lt:
+            # the brick's closed box meets the tight box
+            tlo, thi = tight_box(atoms, tight_fill)
+            a = origin[None, :] + low.astype(np.float64) * h_fine
+            b = origin[None, :] + (low + 8 * f).astype(np.float64) * h_fine
+            near = near | ((a <= thi[None, :]) & (b >= tlo[None, :])).all(axis=1)
+        near = near.reshape(nl, nl, nl)
         up = np.repeat(np.repeat(np.repeat(near, f, 0), f, 1), f, 2)
         level[(level == l) & up] = l + 1
     # 2:1 balance over faces, edges and corners

@@ -186,3 +186,42 @@ def test_far_field_coarsening_is_small(O, orc):
     for k in ("e_pol", "e_ion_flux"):
         assert abs(res["energy"][k] / ref["energy"][k] - 1.0) < 1e-12
     assert abs(res["energy"]["e_ion_surf"] / ref["energy"]["e_ion_surf"] - 1.0) < 1e-3
+
+
+def test_derefined_domain_with_null_bc(O, orc):
+    """Sec. 3.4: a tight box refined around the molecule and coarse cells out
+    to a low perfil make homogeneous Dirichlet values accurate.  Kirkwood
+    sphere (R = 2 A, q = 1 e, eps 2/80, 0.145 M): on a tight domain (perfil
+    50 %) null boundary values miss the ionic energy entirely (error above
+    100 %), Debye-Hueckel values do not (about 13 % at h = 0.5 A); on the
+    de-refined domain (perfil 12.5 %, 1 A far-field cells) null values match
+    the Debye-Hueckel result with a third of the unknowns of a uniform grid
+    over the same box.  E_pol is exact (Gauss) in every case."""
+    lB, kD = orc.units(298.15, 0.145, 80.0)
+    e_pol = 0.5 * (1 / 80.0 - 1 / 2.0) * lB / 2.0
+    e_ion = -0.5 * lB / 80.0 * kD / (1.0 + kD * 2.0)
+    atoms = np.array([[0.0, 0.0, 0.0, 2.0, 1.0]])
+
+    def run(bc, **kw):
+        tree = O.build(atoms, **kw)
+        r = O.solve_problem(atoms, tree, bc=bc, rtol=1e-11)
+        e = r["energy"]
+        assert abs(e["e_pol"] - e_pol) < 1e-9 * abs(e_pol)
+        return tree, len(r["unk_slot"]), (e["e_ion_surf"] + e["e_ion_flux"] - e_ion) / abs(e_ion)
+
+    _, _, tight_null = run(orc.BC_ZERO, h_fine=0.5, h_bulk=0.5, refine_dist=3.0, fill=1.25)
+    _, _, tight_dh = run(orc.BC_DH, h_fine=0.5, h_bulk=0.5, refine_dist=3.0, fill=1.25)
+    tree, unk, deref_null = run(orc.BC_ZERO, h_fine=0.5, h_bulk=4.0, refine_dist=3.0,
+                                fill=1 / 0.15, h_tight=0.5, tight_fill=1.25)
+    assert abs(tight_null) > 1.0 and abs(tight_dh) < 0.2
+    assert abs(deref_null) <= abs(tight_dh)
+    # a coarser far field around the tight box at h_tight (the 2:1 balance
+    # grades the cells brick by brick, 8 cells per brick and level)
+    assert tree.Lmax == 3 and set(np.unique(tree.blevel)) == {2, 3}
+    assert unk < (tree.NL - 1) ** 3 / 2
+    # the tight box lies in bricks of cells no coarser than h_tight
+    tlo, thi = O.tight_box(atoms, 1.25)
+    P = tree.slot_positions()
+    W = tree.world(P)
+    inbox = np.all((W >= tlo) & (W <= thi), axis=1)
+    assert np.all(tree.spacing(tree.blevel)[np.arange(len(P)) // 512][inbox] == 1)
