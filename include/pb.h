@@ -100,7 +100,17 @@ pb_status pb_set_allocator(pb_alloc_fn alloc, pb_free_fn release, void *ctx);
  * n[0] = ceil(fill * extent / (8 h_bulk)) bricks centred on the atoms'
  * bounding box.  Node arrays of an octree use the slot layout: brick b (in
  * Morton order) owns slots 512 b + (8k + j) 8 + i, its low-corner nodes;
- * N = 512 * bricks.  Listed-edge ids are d * N + slot of the low end. */
+ * N = 512 * bricks.  Listed-edge ids are d * N + slot of the low end.
+ *
+ * De-refined octree domain (Sec. 3.4, de-refinement for efficient boundary
+ * conditions): h_tight > 0 makes h_bulk the spacing of the coarse far field
+ * (h_bulk = h_tight times a power of two) and also splits every brick whose
+ * cells are coarser than h_tight and whose box meets the tight box, a cube of
+ * side tight_fill * extent (tight_fill >= 1, e.g. 1.1 for a perfil near 90 %)
+ * centred on the atoms' bounding box; fill can then be large (e.g. 1/0.15,
+ * perfil 15 %), where homogeneous Dirichlet values (PB_BC_ZERO) are accurate.
+ * refine_dist must then be at least 1.5 h_tight instead of 1.5 h_bulk.
+ * h_tight = 0: no tight box (every unrefined brick has cells of h_bulk). */
 typedef struct {
     int32_t kind;
     int32_t n[3];
@@ -108,6 +118,7 @@ typedef struct {
     double h;
     double fill;
     double h_fine, h_bulk, refine_dist;
+    double h_tight, tight_fill;
 } pb_grid_spec;
 
 /* Physical parameters (Sec. 2.1, 2.3).  eps_in/eps_out relative
@@ -153,15 +164,23 @@ typedef struct {
  *               of Eq. energy_ion);
  *   e_ion_surf  1/2 sum_e phi(r_e) h^2 Psi_e / (4 pi)  (first integral of
  *               Eq. energy_ion on the staircase dual faces of the flux edges,
- *               phi(r_e) from Eq. phi0) -- a stand-in for the paper's
- *               triangulated surface;
+ *               phi(r_e) from Eq. phi0) -- a quadrature of the first integral
+ *               with a cheaper surface than the paper's;
  *   e_total     sum of the four;
- *   flux_charge sum_e F_e / (4 pi l_B): the enclosed charge by Gauss' law.
+ *   flux_charge sum_e F_e / (4 pi l_B): the enclosed charge by Gauss' law;
+ *   e_ion_mc    1/2 sum_e T_e phi(r_e) Psi^n_e / (4 pi): the first integral
+ *               of Eq. energy_ion as Sec. 3.3.2 takes it, on the surface
+ *               re-triangulated by marching cubes through the intersection
+ *               points r_e, T_e = sum of T_j/3 over the triangles with vertex
+ *               r_e, Psi^n_e with the analytic ball normal at r_e, phi(r_e)
+ *               from Eq. phi0 (uniform grids; 0 on octree grids).  The paper's
+ *               E_ion is e_ion_mc + e_ion_flux.
  * F_e = W_e (phi_in - phi_out) over flux edges (endpoints in different
  * media), Phi_e = sum_i q_i/|r_e - r_i|, Psi_e = sum_i q_i (r_e - r_i).n_e /
  * |r_e - r_i|^3, n_e the unit edge direction from the inside endpoint. */
 typedef struct {
     double e_coul, e_pol, e_ion_surf, e_ion_flux, e_total, flux_charge;
+    double e_ion_mc;
 } pb_energy_terms;
 
 typedef struct {
@@ -205,6 +224,13 @@ enum {
     PB_ARR_OCT_KIND,     /* uint8  [N] octree: 0 unknown with a 7-point row, 1
                             boundary, 2 hanging, 3 unknown next to a level
                             change (explicit row)                           */
+    PB_ARR_MC_WEIGHT,    /* double [n_cross] uniform grids: T_e, the sum of T_j/3
+                            over the marching-cubes triangles with vertex r_e
+                            (0 on edges whose endpoints share a medium)       */
+    PB_ARR_MC_NORMAL,    /* double [3*n_cross] uniform grids: analytic outward
+                            unit normal of the ball surface at r_e            */
+    PB_ARR_PSI_N,        /* double [n_cross] uniform grids: Psi along that
+                            normal                                            */
     PB_ARR_COUNT
 };
 
@@ -267,9 +293,18 @@ pb_status pb_get_array(const pb_grid *g, const pb_system *s, int32_t which, void
  * used by the inner solver). */
 pb_status pb_apply(pb_system *s, int32_t precision, const void *x, void *y, void *stream);
 
-/* pb_solve_batch -- solve n independent systems (different molecules and
- * grid sizes) with one persistent, CUDA-graph-launched mixed-precision
- * solver; stats has n entries.  All systems must live on the same device. */
+/* pb_solve_batch -- solve n independent systems (different molecules, grid
+ * sizes, uniform or octree) together: the CG solve of Eq. matrixequation
+ * (Sec. 4) with FP32 inner iterations and FP64 iterative refinement.  PB_MIXED:
+ * every system holds a slot of one launch table of persistent TMA-staged PCG
+ * kernels, replayed as one captured CUDA graph; each system's refinement step
+ * is decided on the device as soon as its own inner solve ends (the
+ * continuous-batching engine below, with capacity n).  PB_FP64: plain PCG,
+ * one system after the other.  stats has n entries (each system's status;
+ * the call returns the worst).  Each system's result is bit-identical to its
+ * own pb_solve with the same tuning.  All systems must live on the same
+ * device, and none may appear twice (PB_ERR_ARG).  time_budget_s > 0 stops
+ * the batch at the budget: unfinished systems report PB_ERR_TIMEOUT. */
 pb_status pb_solve_batch(pb_system *const *systems, int32_t n, const pb_solve_opts *opts,
                          void *stream, pb_solve_stats *stats);
 

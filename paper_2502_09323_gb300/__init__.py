@@ -116,13 +116,17 @@ class GridSpec:
 class OctreeSpec:
     """Octree brick grid: cells h_bulk / 2^l down to h_fine, refined within
     refine_dist of the atom spheres.  n0 = 0 places n0^3 coarse bricks
-    automatically (cube of fill x extent); n0 > 0 uses ``origin``."""
+    automatically (cube of fill x extent); n0 > 0 uses ``origin``.
+    h_tight > 0: de-refined domain, h_bulk is the far-field spacing and the
+    tight box (tight_fill x extent) is refined to at least h_tight."""
     h_fine: float = 0.25
     h_bulk: float = 1.0
     refine_dist: float = 3.0
     fill: float = 1.5
     n0: int = 0
     origin: tuple = (0.0, 0.0, 0.0)
+    h_tight: float = 0.0
+    tight_fill: float = 1.1
 
     def c(self) -> N.GridSpecC:
         s = N.GridSpecC()
@@ -132,6 +136,7 @@ class OctreeSpec:
             s.origin[d] = float(self.origin[d])
         s.fill = float(self.fill)
         s.h_fine, s.h_bulk, s.refine_dist = float(self.h_fine), float(self.h_bulk), float(self.refine_dist)
+        s.h_tight, s.tight_fill = float(self.h_tight), float(self.tight_fill)
         return s
 
 
@@ -299,6 +304,9 @@ _ARRAYS = {
     "psi_surf": (N.ARR_PSI_SURF, np.float64, "nc"),
     "oct_bricks": (N.ARR_OCT_BRICKS, np.int32, "nb4"),
     "oct_kind": (N.ARR_OCT_KIND, np.uint8, "N"),
+    "mc_weight": (N.ARR_MC_WEIGHT, np.float64, "nc"),
+    "mc_normal": (N.ARR_MC_NORMAL, np.float64, "nc3"),
+    "psi_n": (N.ARR_PSI_N, np.float64, "nc"),
 }
 
 

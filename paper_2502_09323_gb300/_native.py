@@ -17,7 +17,7 @@ HOST, DEVICE = 0, 1
 CT_BOUNDARY, CT_SURFACE, CT_PAIRS, CT_ALL = 1, 2, 4, 7
 (ARR_INSIDE, ARR_CROSS_ID, ARR_CROSS_ALPHA, ARR_CROSS_RP, ARR_CROSS_SIGN, ARR_WX, ARR_WY, ARR_WZ,
  ARR_KAPPA, ARR_DIAG, ARR_RHS, ARR_BC, ARR_PHI, ARR_PHI_SURF, ARR_PSI_SURF, ARR_OCT_BRICKS,
- ARR_OCT_KIND) = range(17)
+ ARR_OCT_KIND, ARR_MC_WEIGHT, ARR_MC_NORMAL, ARR_PSI_N) = range(20)
 GRID_UNIFORM, GRID_OCTREE = 0, 1
 
 
@@ -30,7 +30,8 @@ class PBError(RuntimeError):
 class GridSpecC(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n", C.c_int32 * 3), ("origin", C.c_double * 3),
                 ("h", C.c_double), ("fill", C.c_double), ("h_fine", C.c_double),
-                ("h_bulk", C.c_double), ("refine_dist", C.c_double)]
+                ("h_bulk", C.c_double), ("refine_dist", C.c_double),
+                ("h_tight", C.c_double), ("tight_fill", C.c_double)]
 
 
 class ParamsC(C.Structure):
@@ -51,7 +52,8 @@ class SolveStatsC(C.Structure):
 
 class EnergyC(C.Structure):
     _fields_ = [("e_coul", C.c_double), ("e_pol", C.c_double), ("e_ion_surf", C.c_double),
-                ("e_ion_flux", C.c_double), ("e_total", C.c_double), ("flux_charge", C.c_double)]
+                ("e_ion_flux", C.c_double), ("e_total", C.c_double), ("flux_charge", C.c_double),
+                ("e_ion_mc", C.c_double)]
 
 
 class GridInfoC(C.Structure):

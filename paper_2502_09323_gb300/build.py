@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
           "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math", "-I", INCLUDE]
 # translation units whose FP64 results must be reproducible to the bit
-NO_FMA = {"grid.cu", "assemble.cu"}
+NO_FMA = {"grid.cu", "assemble.cu", "surface.cu"}
 
 
 def sources() -> list[str]:

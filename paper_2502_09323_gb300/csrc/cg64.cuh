@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(cg64::NT, 2) k_cg64_dir(cg64::DirArgs A) {
 
 // Update kernel: streams the interior planes (boundary rows and padding hold
 // zeros, so they need no test), two slots per thread and loop step.
-__global__ void __launch_bounds__(cg64::UNT) k_cg64_upd(cg64::UpdArgs A) {
+__global__ void __launch_bounds__(cg64::UNT, 4) k_cg64_upd(cg64::UpdArgs A) {
     using namespace cg64;
     __shared__ double sred[UNT / 32];
     if (A.st->done) return;

@@ -2,7 +2,8 @@
 // Coulomb / Debye-Hueckel boundary condition (Sec. 2.3).
 //
 //   Phi_t = sum_i q_i exp(-k r_ti) / r_ti          (k = 0: Coulomb)
-//   Psi_t = sum_i q_i (r_t - r_i).n_t / r_ti^3      (dipole kernel, n_t = +-e_d)
+//   Psi_t = sum_i q_i (r_t - r_i).n_t / r_ti^3      (dipole kernel, n_t = +-e_d,
+//                                                    or the analytic surface normal)
 //
 // FP32 tiled kernel: sources staged in shared memory 256 at a time; each
 // position is stored as an FP32 pair (hi + lo) relative to the grid centre so
@@ -58,6 +59,7 @@ struct TargetDesc {
     const double *rp;
     const long long *ids;
     const int8_t *sign;
+    const double *nrm2; // optional second normal per target (PSI2): 3 per target
     long long count;
 };
 
@@ -102,6 +104,7 @@ __device__ __forceinline__ void boundary_node(const GridGeo &g, long long b, lon
 struct TgtLoad {
     float h[3], l[3];
     float n[3];     // unit normal for Psi (surface targets)
+    float n2[3];    // second normal (the analytic surface normal) when given
     bool active;    // contributes (flux edge / valid index)
 };
 
@@ -110,6 +113,7 @@ __device__ __forceinline__ TgtLoad load_target(const TargetDesc &T, long long t)
     double p[3] = {0.0, 0.0, 0.0};
     r.active = t < T.count;
     r.n[0] = r.n[1] = r.n[2] = 0.f;
+    r.n2[0] = r.n2[1] = r.n2[2] = 0.f;
     if (r.active) {
         if (T.kind == TK_BOUNDARY) {
             long long i, j, k;
@@ -117,11 +121,13 @@ __device__ __forceinline__ TgtLoad load_target(const TargetDesc &T, long long t)
             p[0] = T.g.o[0] + (double)i * T.g.h;
             p[1] = T.g.o[1] + (double)j * T.g.h;
             p[2] = T.g.o[2] + (double)k * T.g.h;
-        } else if (T.kind == TK_SURFACE) {
+        } else {
             int sg = T.sign[t];
             if (sg == 0) r.active = false;
             int d = (int)(T.ids[t] / T.g.N);
             r.n[d] = (float)sg;
+            if (T.nrm2)
+                for (int d = 0; d < 3; ++d) r.n2[d] = (float)T.nrm2[3 * t + d];
             p[0] = T.rp[3 * t];
             p[1] = T.rp[3 * t + 1];
             p[2] = T.rp[3 * t + 2];
@@ -149,32 +155,35 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 v) {
 }
 
 // out_phi[t] = scale * sum_i q_i exp(-k r)/r; out_psi[t] = sum_i q_i (r.n)/r^3
-// (PSI only for surface targets).  Self pairs (r == 0) are skipped.  Each
+// (PSI only for surface targets); with PSI2 also out_psi2[t] along the
+// target's second normal, from the same pairs.  Self pairs (r == 0) are skipped.  Each
 // thread holds two targets in the two halves of FP32x2 registers; the
 // sources are staged in shared memory already duplicated into (v, v) pairs.
 static_assert(NB_TPT == 2, "two targets per thread, one per FP32x2 half");
-template <bool PSI, bool SCREEN>
+template <bool PSI, bool SCREEN, bool PSI2 = false>
 __global__ void __launch_bounds__(NB_THREADS)
 k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__ slo,
         long long ns, float kscr, double scale, double *__restrict__ out_phi,
-        double *__restrict__ out_psi) {
+        double *__restrict__ out_psi, double *__restrict__ out_psi2 = nullptr) {
     // per source: (hx,hx,hy,hy) (hz,hz,q,q) (lx,lx,ly,ly) (lz,lz,0,0)
     __shared__ float4 sp4[NB_THREADS][4];
     long long t0 = ((long long)blockIdx.x * NB_THREADS * NB_TPT) + threadIdx.x;
     TgtLoad tg[NB_TPT];
-    double acc_phi[NB_TPT], acc_psi[NB_TPT];
+    double acc_phi[NB_TPT], acc_psi[NB_TPT], acc_psi2[NB_TPT];
 #pragma unroll
     for (int u = 0; u < NB_TPT; ++u) {
         tg[u] = load_target(T, t0 + (long long)u * NB_THREADS);
         acc_phi[u] = 0.0;
         acc_psi[u] = 0.0;
+        acc_psi2[u] = 0.0;
     }
-    float2 th[3], tl[3], tn[3];
+    float2 th[3], tl[3], tn[3], tn2[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         th[d] = make_float2(tg[0].h[d], tg[1].h[d]);
         tl[d] = make_float2(tg[0].l[d], tg[1].l[d]);
         tn[d] = make_float2(tg[0].n[d], tg[1].n[d]);
+        tn2[d] = make_float2(tg[0].n2[d], tg[1].n2[d]);
     }
     for (long long base = 0; base < ns; base += NB_THREADS) {
         long long si = base + threadIdx.x;
@@ -190,7 +199,8 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
         sp4[threadIdx.x][3] = make_float4(b.z, b.z, 0.f, 0.f);
         __syncthreads();
         int m = (int)min((long long)NB_THREADS, ns - base);
-        float2 sp = bc2(0.f), cp = bc2(0.f), sq = bc2(0.f), cq = bc2(0.f);
+        float2 sp = bc2(0.f), cp = bc2(0.f), sq = bc2(0.f), cq = bc2(0.f), s2 = bc2(0.f),
+               c2 = bc2(0.f);
 #pragma unroll 4
         for (int q = 0; q < m; ++q) {
             const float4 p0 = sp4[q][0], p1 = sp4[q][1], p2 = sp4[q][2], p3 = sp4[q][3];
@@ -212,7 +222,13 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
             if (PSI) {
                 const float2 dn =
                     __ffma2_rn(dz, tn[2], __ffma2_rn(dy, tn[1], __fmul2_rn(dx, tn[0])));
-                kahan_add2(sq, cq, __fmul2_rn(__fmul2_rn(v, dn), __fmul2_rn(ri, ri)));
+                const float2 vr2 = __fmul2_rn(v, __fmul2_rn(ri, ri));
+                kahan_add2(sq, cq, __fmul2_rn(vr2, dn));
+                if (PSI2) {
+                    const float2 dn2 =
+                        __ffma2_rn(dz, tn2[2], __ffma2_rn(dy, tn2[1], __fmul2_rn(dx, tn2[0])));
+                    kahan_add2(s2, c2, __fmul2_rn(vr2, dn2));
+                }
             }
         }
         acc_phi[0] += (double)sp.x - (double)cp.x;
@@ -220,6 +236,10 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
         if (PSI) {
             acc_psi[0] += (double)sq.x - (double)cq.x;
             acc_psi[1] += (double)sq.y - (double)cq.y;
+        }
+        if (PSI2) {
+            acc_psi2[0] += (double)s2.x - (double)c2.x;
+            acc_psi2[1] += (double)s2.y - (double)c2.y;
         }
     }
 #pragma unroll
@@ -233,6 +253,7 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
         } else {
             out_phi[t] = tg[u].active ? scale * acc_phi[u] : 0.0;
             if (PSI) out_psi[t] = tg[u].active ? acc_psi[u] : 0.0;
+            if (PSI2) out_psi2[t] = tg[u].active ? acc_psi2[u] : 0.0;
         }
     }
 }
@@ -354,6 +375,7 @@ TargetDesc make_desc(pb_system *sys, int kind) {
     T.rp = g->crp;
     T.ids = g->cid;
     T.sign = g->csign;
+    T.nrm2 = nullptr;
     T.count = 0;
     return T;
 }
@@ -387,9 +409,22 @@ pb_status nbody_surface(pb_system *sys, cudaStream_t s) {
     if (st != PB_OK) return st;
     TargetDesc T = make_desc(sys, TK_SURFACE);
     T.count = g->ncross;
-    k_nbody<true, false><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
-        T, hi, lo, g->na, 0.f, 1.0, sys->Phi, sys->Psi);
-    PB_LAUNCH_CHECK();
+    if (g->is_oct) {
+        k_nbody<true, false><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
+            T, hi, lo, g->na, 0.f, 1.0, sys->Phi, sys->Psi);
+        PB_LAUNCH_CHECK();
+    } else {
+        // the re-triangulated surface (vertex weights, analytic normals);
+        // Psi along those normals comes from the same pairs as Phi and Psi
+        // (first integral of Eq. energy_ion, Sec. 3.3.2)
+        if (!sys->PsiN) sys->PsiN = (double *)dalloc(sizeof(double) * nc, s);
+        if (!sys->PsiN) return PB_ERR_OOM;
+        if ((st = mc_surface(sys, s)) != PB_OK) return st;
+        T.nrm2 = sys->mc_n;
+        k_nbody<true, false, true><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
+            T, hi, lo, g->na, 0.f, 1.0, sys->Phi, sys->Psi, sys->PsiN);
+        PB_LAUNCH_CHECK();
+    }
     dfree(hi, s);
     dfree(lo, s);
     return PB_OK;

@@ -229,9 +229,12 @@ __global__ void __launch_bounds__(OT) k_oct_bbox(const double *__restrict__ atom
 // dist of the box can pass the test, so the box scans the atom cell list
 // over the cells that meet the box grown by reach (one cell of margin on
 // each side); the flag is an OR over atoms, so the order does not matter.
+// On a de-refined domain the boxes of the levels coarser than h_tight that
+// meet the tight box [tlo, thi] are near too.
 __global__ void k_oct_near(const double *__restrict__ atoms, long long na, OctDev t, int level,
                            double dist, double reach, CellList cl,
-                           const uint8_t *__restrict__ parent_near, uint8_t *__restrict__ near) {
+                           const uint8_t *__restrict__ parent_near, uint8_t *__restrict__ near,
+                           bool tight, double3 tlo, double3 thi) {
     const int nl = t.n0 << level;
     const long long nbox = (long long)nl * nl * nl;
     const long long q = blockIdx.x * (long long)OT + threadIdx.x;
@@ -250,6 +253,11 @@ __global__ void k_oct_near(const double *__restrict__ atoms, long long na, OctDe
     for (int d = 0; d < 3; ++d) {
         a[d] = wpos(t, d, lo[d]);
         b[d] = wpos(t, d, lo[d] + side);
+    }
+    if (tight && a[0] <= thi.x && b[0] >= tlo.x && a[1] <= thi.y && b[1] >= tlo.y &&
+        a[2] <= thi.z && b[2] >= tlo.z) {
+        near[q] = 1;
+        return;
     }
     const double *X = atoms, *Y = atoms + na, *Z = atoms + 2 * na, *R = atoms + 3 * na;
     int c0[3], c1[3];
@@ -1518,13 +1526,14 @@ k_oct_energy(const long long *__restrict__ ids, const long long *__restrict__ sl
             acc->S = tot[0];
             acc->I = tot[1];
             acc->F = tot[2];
-            pb_energy_terms o;
+            pb_energy_terms o{};
             o.e_coul = (lB / eps_in) * 0.5 * acc->ecoul_sum;
             o.e_pol = 0.5 * (1.0 / eps_out - 1.0 / eps_in) * tot[0] / fourpi;
             o.e_ion_flux = -0.5 * (1.0 / eps_out) * tot[0] / fourpi;
             o.e_ion_surf = 0.5 * tot[1] / fourpi;
             o.e_total = o.e_coul + o.e_pol + o.e_ion_surf + o.e_ion_flux;
             o.flux_charge = tot[2] / (fourpi * lB);
+            o.e_ion_mc = 0.0;  // the re-triangulated surface is built on uniform grids
             acc->out = o;
             acc->counter = 0;
         }
@@ -1601,9 +1610,34 @@ pb_status oct_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
         set_error("atoms: non-finite value or non-positive radius");
         return PB_ERR_ARG;
     }
-    if (!(dist >= hinfo.rmax) || !(dist >= hf) || !(dist >= 1.5 * hb)) {
-        set_error("octree: refine_dist must be at least the largest radius, h_fine and 1.5 h_bulk");
+    // de-refined domain: levels coarser than h_tight are split inside the tight box
+    int Lt = 0;
+    double h_near = hb;
+    if (spec->h_tight > 0.0) {
+        while (Lt < Lmax && spec->h_tight * (double)(1 << Lt) < hb) ++Lt;
+        if (spec->h_tight * (double)(1 << Lt) != hb || !(spec->tight_fill >= 1.0)) {
+            set_error("octree: h_bulk must be h_tight times a power of two, h_tight at least "
+                      "h_fine, and tight_fill at least 1");
+            return PB_ERR_ARG;
+        }
+        h_near = spec->h_tight;
+    }
+    if (!(dist >= hinfo.rmax) || !(dist >= hf) || !(dist >= 1.5 * h_near)) {
+        set_error("octree: refine_dist must be at least the largest radius, h_fine and 1.5 h_bulk "
+                  "(1.5 h_tight on a de-refined domain)");
         return PB_ERR_ARG;
+    }
+    double3 tlo = make_double3(0.0, 0.0, 0.0), thi = tlo;
+    if (Lt > 0) {
+        double ext = 0.0;
+        for (int d = 0; d < 3; ++d) ext = std::max(ext, hinfo.hi[d] - hinfo.lo[d]);
+        const double half = 0.5 * spec->tight_fill * ext;
+        tlo = make_double3(0.5 * (hinfo.lo[0] + hinfo.hi[0]) - half,
+                           0.5 * (hinfo.lo[1] + hinfo.hi[1]) - half,
+                           0.5 * (hinfo.lo[2] + hinfo.hi[2]) - half);
+        thi = make_double3(0.5 * (hinfo.lo[0] + hinfo.hi[0]) + half,
+                           0.5 * (hinfo.lo[1] + hinfo.hi[1]) + half,
+                           0.5 * (hinfo.lo[2] + hinfo.hi[2]) + half);
     }
     OctDev &t = g->ot;
     t.hf = hf;
@@ -1653,7 +1687,8 @@ pb_status oct_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
         if (!near[l] || !split[l]) return PB_ERR_OOM;
         k_oct_near<<<cdiv(nl * nl * nl, OT), OT, 0, s>>>(g->atoms, na, t, l, dist,
                                                           hinfo.rmax + dist, g->cells,
-                                                          l > 0 ? near[l - 1] : nullptr, near[l]);
+                                                          l > 0 ? near[l - 1] : nullptr, near[l],
+                                                          l < Lt, tlo, thi);
         PB_LAUNCH_CHECK();
         np.p[l] = near[l];
         sp.p[l] = split[l];

@@ -160,6 +160,7 @@ struct CgState {
 
 struct EnergyAcc {
     double S, I, F;  // sum F*Phi, sum phi(rp) h^2 Psi, sum F
+    double Imc;      // sum W phi(rp) Psi_n over the re-triangulated surface
     double ecoul_sum;
     pb_energy_terms out;
     unsigned int counter;
@@ -192,6 +193,9 @@ struct pb_system {
     pbg::CgState *st;
     pbg::CgState *h_st; // pinned host mirror
     double *Phi, *Psi;  // [ncross]
+    // uniform grids: re-triangulated surface (vertex weights T_j/3, analytic
+    // unit normals) and Psi along those normals, [ncross] / [3 ncross]
+    double *mc_w, *mc_n, *PsiN;
     pbg::EnergyAcc *eacc;
     pb_energy_terms *h_energy;  // pinned
     int solved, have_surface, have_pairs;
@@ -215,6 +219,9 @@ pb_status fill_kappa(const pb_system *sys, double *dst, cudaStream_t s);
 pb_status nbody_boundary(pb_system *sys, cudaStream_t s);
 pb_status nbody_surface(pb_system *sys, cudaStream_t s);
 pb_status nbody_pairs(pb_system *sys, cudaStream_t s);
+
+// ------------------------------------------------------------ surface.cu --
+pb_status mc_surface(pb_system *sys, cudaStream_t s);
 
 // -------------------------------------------------------------- solve.cu --
 pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve_stats *st);

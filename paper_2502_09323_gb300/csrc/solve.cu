@@ -1587,298 +1587,73 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
 
 namespace pbg {
 
-// Batched mixed-precision solve: every system's FP32 PCG runs inside the
-// same TMA-staged launches (one launch table over all systems), replayed as a
-// CUDA graph of `chunk` iterations; the FP64 refinement steps run per system
-// between inner solves.  A system's arithmetic is the same as in pb_solve
-// with the same tuning, so its result does not depend on the batch.
+#include "engine.cuh"
+
+// Batched mixed-precision solve through the continuous-batching engine: every
+// system takes a slot of one launch table, whose PCG iterations run as
+// replays of one captured graph, and each system's FP64 refinement steps are
+// decided on the device (k_ir_step) as soon as its own inner solve ends, so
+// no system waits for another's.  The host only watches the pinned state
+// mirror.  A system's arithmetic is the same as in pb_solve with the same
+// tuning, so its result does not depend on the batch (uniform and octree
+// systems alike).
 pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, cudaStream_t s,
                       pb_solve_stats *stats) {
     const double t_start = now_s();
     const double deadline = o->time_budget_s > 0.0 ? t_start + o->time_budget_s : 0.0;
-    const int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
-    const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
-    const double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
-    const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
-    const int chunk = 8;  // PCG iterations per graph replay
-    pb_status rc = PB_OK;
-
-    std::vector<int> kc(n);
-    for (int i = 0; i < n; ++i) {
-        pb_system *sys = systems[i];
-        if ((rc = ensure_solver_ws(sys, PB_MIXED, s)) != PB_OK) return rc;
-        if ((rc = build_tma_state(sys)) != PB_OK) return rc;
-        Tuning tune;
-        if ((rc = autotune(sys, PB_MIXED, s, &tune)) != PB_OK) return rc;
-        kc[i] = tune.variant == 1 ? std::max(tune.kc, 4) : 8;
-    }
-
-    // contiguous CG states so one copy reports every system
-    CgState *bst = (CgState *)dalloc(sizeof(CgState) * n, s);
-    CgState *hst = nullptr;
-    if (!bst || cudaMallocHost((void **)&hst, sizeof(CgState) * 3 * n) != cudaSuccess) {
-        dfree(bst, s);
-        set_error("batch state allocation failed");
-        return PB_ERR_OOM;
-    }
-    PB_CUDA_TRY(cudaMemsetAsync(bst, 0, sizeof(CgState) * n, s));
-    std::vector<CgState *> orig(n);
-    std::vector<tma::SysEntry> tab(n);
-    int total = 0;
-    for (int i = 0; i < n; ++i) {
-        pb_system *sys = systems[i];
-        orig[i] = sys->st;
-        sys->st = bst + i;
-        TmaState *t = (TmaState *)sys->tma;
-        tab[i] = t->host;
-        tma_entry_geometry(tab[i], sys->pad, kc[i]);
-        tab[i].item_base = total;
-        tab[i].st = bst + i;
-        total += tab[i].nitems;
-    }
-    tma::SysEntry *dtab = (tma::SysEntry *)dalloc(sizeof(tma::SysEntry) * n, s);
-    unsigned int *queue = (unsigned int *)dalloc(4 * sizeof(unsigned int), s);
-    cudaStream_t cs = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_chunk[2] = {nullptr, nullptr};
-    std::vector<double> fn2(n, 0.0), res2(n, 0.0), rz(n, 0.0);
-    std::vector<int> iters(n, 0), outer(n, 1), status(n, PB_OK), stagnant(n, 0);
-    auto fail = [&](pb_status r) {
-        rc = r;
-        return r;
-    };
-    do {
-        if (!dtab || !queue) {
-            fail(PB_ERR_OOM);
-            break;
-        }
-        if (cudaMemcpyAsync(dtab, tab.data(), sizeof(tma::SysEntry) * n, cudaMemcpyHostToDevice, s) !=
-                cudaSuccess ||
-            cudaMemsetAsync(queue, 0, 4 * sizeof(unsigned int), s) != cudaSuccess) {
-            fail(PB_ERR_CUDA);
-            break;
-        }
-        // initial residuals (phi = boundary values, interior 0)
-        for (int i = 0; i < n && rc == PB_OK; ++i) {
-            pb_system *sys = systems[i];
-            if (cudaMemcpyAsync(sys->phi, sys->bc, sizeof(double) * sys->g->geo.N,
-                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                fail(PB_ERR_CUDA);
-            else
-                rc = residual(sys, true, s);
-        }
-        if (rc != PB_OK) break;
-        if (cudaMemcpyAsync(hst, bst, sizeof(CgState) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            fail(PB_ERR_CUDA);
-            break;
-        }
-        for (int i = 0; i < n; ++i) {
-            fn2[i] = res2[i] = hst[i].res64;
-            rz[i] = hst[i].rz64;
-        }
-        // the inner iteration chunk, captured once on a private stream
-        const dim3 grid = tma_grid(systems[0]->pad, 8);
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ev_chunk[0], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ev_chunk[1], cudaEventDisableTiming) != cudaSuccess) {
-            fail(PB_ERR_CUDA);
-            break;
-        }
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            fail(PB_ERR_CUDA);
-            break;
-        }
-        for (int c = 0; c < chunk; ++c) {
-            tma_launch<MODE_P>(dtab, n, total, queue, grid, cs, &tab[0]);
-            tma_launch<MODE_U>(dtab, n, total, queue, grid, cs, &tab[0]);
-        }
-        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess ||
-            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("capturing the batched PCG chunk failed");
-            fail(PB_ERR_CUDA);
-            break;
-        }
-        for (;;) {
-            // systems still refining
-            std::vector<int> act;
-            for (int i = 0; i < n; ++i) {
-                if (status[i] != PB_OK) continue;
-                if (!(fn2[i] > 0.0) || res2[i] <= rtol * rtol * fn2[i]) continue;
-                if (outer[i] > max_outer || iters[i] >= max_iter) {
-                    status[i] = PB_ERR_NOCONV;
-                    continue;
-                }
-                act.push_back(i);
-            }
-            if (act.empty()) break;
-            CgState *stage = hst + 2 * n;  // third mirror: staging of the initial states
-            for (int i = 0; i < n; ++i) {
-                CgState h{};
-                h.done = 1;
-                stage[i] = h;
-            }
-            for (int i : act) {
-                const double rel = sqrt(res2[i] / fn2[i]);
-                double itol = std::max(inner_rtol, 0.5 * rtol / rel);
-                if (itol > 0.5) itol = 0.5;
-                CgState &h = stage[i];
-                h.rho = rz[i];
-                h.rr0 = h.rr = res2[i];
-                h.rr_stop = itol * itol * res2[i];
-                h.max_iter = max_iter - iters[i];
-                h.done = 0;
-                const size_t b32 = sizeof(float) * (size_t)systems[i]->pad.Np;
-                if (cudaMemsetAsync(systems[i]->d32, 0, b32, s) != cudaSuccess ||
-                    cudaMemsetAsync(systems[i]->pa32, 0, b32, s) != cudaSuccess)
-                    fail(PB_ERR_CUDA);
-            }
-            if (rc != PB_OK) break;
-            if (cudaMemcpyAsync(bst, stage, sizeof(CgState) * n, cudaMemcpyHostToDevice, s) !=
-                    cudaSuccess ||
-                cudaEventRecord(ev_in, s) != cudaSuccess || cudaStreamWaitEvent(cs, ev_in, 0) != cudaSuccess) {
-                fail(PB_ERR_CUDA);
-                break;
-            }
-            // replay chunks until every system's inner solve is done (two in flight)
-            long long max_chunks = (long long)max_iter / chunk + 4;
-            long long issued = 0;
-            int slot = 0;
-            auto issue = [&](int sl) -> bool {
-                return note_launch(2 * chunk), cudaGraphLaunch(exec, cs) == cudaSuccess &&
-                       cudaMemcpyAsync(hst + sl * n, bst, sizeof(CgState) * n, cudaMemcpyDeviceToHost, cs) ==
-                           cudaSuccess &&
-                       cudaEventRecord(ev_chunk[sl], cs) == cudaSuccess;
-            };
-            if (!issue(0) || !issue(1)) {
-                fail(PB_ERR_CUDA);
-                break;
-            }
-            issued = 2;
-            bool timed_out = false;
-            for (;;) {
-                if (cudaEventSynchronize(ev_chunk[slot]) != cudaSuccess) {
-                    fail(PB_ERR_CUDA);
-                    break;
-                }
-                bool all = true;
-                for (int i : act) all = all && hst[slot * n + i].done;
-                if (all) break;
-                if (deadline > 0.0 && now_s() > deadline) {
-                    timed_out = true;
-                    break;
-                }
-                if (++issued > max_chunks) {
-                    set_error("batched PCG state stopped advancing");
-                    fail(PB_ERR_CUDA);
-                    break;
-                }
-                if (!issue(slot)) {
-                    fail(PB_ERR_CUDA);
-                    break;
-                }
-                slot ^= 1;
-            }
-            if (rc != PB_OK) break;
-            if (cudaEventRecord(ev_out, cs) != cudaSuccess || cudaStreamWaitEvent(s, ev_out, 0) != cudaSuccess) {
-                fail(PB_ERR_CUDA);
-                break;
-            }
-            // FP64 refinement step of every active system
-            if (cudaMemcpyAsync(hst, bst, sizeof(CgState) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess) {
-                fail(PB_ERR_CUDA);
-                break;
-            }
-            std::vector<int> inner_it(n, 0), dev_status(n, 0);
-            for (int i : act) {
-                inner_it[i] = hst[i].iter;
-                dev_status[i] = hst[i].status;
-            }
-            for (int i : act) {
-                pb_system *sys = systems[i];
-                const GridGeo &g = sys->g->geo;
-                // an aborted inner solve's correction is incomplete: not promoted
-                if (dev_status[i] != 3) {
-                    k_promote<float><<<cdiv(g.N, 256), 256, 0, s>>>(sys->phi, sys->d32, g, sys->pad);
-                    note_launch(1);
-                }
-                if ((rc = residual(sys, true, s)) != PB_OK) break;
-            }
-            if (rc != PB_OK) break;
-            if (cudaMemcpyAsync(hst, bst, sizeof(CgState) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess) {
-                fail(PB_ERR_CUDA);
-                break;
-            }
-            for (int i : act) {
-                if (dev_status[i] == 3) {
-                    set_error("a device-side wait reached its limit in the FP32 PCG kernels");
-                    status[i] = PB_ERR_TIMEOUT;
-                }
-                iters[i] += inner_it[i];
-                const double prev = res2[i];
-                res2[i] = hst[i].res64;
-                rz[i] = hst[i].rz64;
-                ++outer[i];
-                if (res2[i] > 0.25 * prev) {
-                    if (++stagnant[i] >= 3) status[i] = PB_ERR_NOCONV;
-                } else {
-                    stagnant[i] = 0;
-                }
-                if (timed_out && status[i] == PB_OK && res2[i] > rtol * rtol * fn2[i])
-                    status[i] = PB_ERR_TIMEOUT;
-            }
-            if (timed_out) break;
-        }
-    } while (false);
-
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    cudaStreamSynchronize(s);
-    if (cs) {
-        cudaStreamSynchronize(cs);
-        cudaStreamDestroy(cs);
-    }
-    for (cudaEvent_t e : {ev_in, ev_out, ev_chunk[0], ev_chunk[1]})
-        if (e) cudaEventDestroy(e);
-    // each system keeps its own state record again
-    for (int i = 0; i < n; ++i) {
-        pb_system *sys = systems[i];
-        if (rc == PB_OK) cudaMemcpyAsync(orig[i], bst + i, sizeof(CgState), cudaMemcpyDeviceToDevice, s);
-        sys->st = orig[i];
-        sys->fnorm2 = fn2[i];
-        if (rc == PB_OK) sys->solved = 1;
-        if (stats) {
-            pb_solve_stats &st = stats[i];
-            st.status = rc != PB_OK ? rc : status[i];
-            st.iters_inner = iters[i];
-            st.iters_outer = outer[i];
-            st.kc = kc[i] + 1000;
-            st.true_rel_res = fn2[i] > 0.0 ? sqrt(res2[i] / fn2[i]) : 0.0;
-            st.seconds = now_s() - t_start;
-            const GridGeo &g = sys->g->geo;
-            st.dof = (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2);
-            st.model_bytes = (long long)iters[i] * st.dof * (8 * 4 + 2) + (long long)outer[i] * g.N * 64;
-        }
-    }
-    cudaStreamSynchronize(s);
-    dfree(dtab, s);
-    dfree(queue, s);
-    dfree(bst, s);
-    cudaStreamSynchronize(s);
-    cudaFreeHost(hst);
+    pb_engine *eh = nullptr;
+    pb_status rc = engine_create(systems[0]->g->device, n, o, &eh);
     if (rc != PB_OK) return rc;
+    std::map<long long, int> index;
+    std::vector<int> got(n, 0);
+    for (int i = 0; i < n && rc == PB_OK; ++i) {
+        long long t = 0;
+        rc = engine_submit(eh, systems[i], s, &t);
+        if (rc == PB_OK) index[t] = i;
+    }
+    int left = rc == PB_OK ? n : 0;
+    bool timed_out = false;
+    std::vector<pb_engine_result> out(std::max(n, 1));
+    while (left > 0) {
+        double wait = 0.05;
+        if (deadline > 0.0) {
+            const double rem = deadline - now_s();
+            if (rem <= 0.0) {
+                timed_out = true;
+                break;
+            }
+            wait = std::min(wait, rem);
+        }
+        int k = 0;
+        pb_status r = engine_wait(eh, wait, out.data(), n, &k);
+        if (r != PB_OK) {
+            rc = r;
+            break;
+        }
+        for (int q = 0; q < k; ++q) {
+            auto it = index.find(out[q].ticket);
+            if (it == index.end()) continue;
+            const int i = it->second;
+            stats[i] = out[q].stats;
+            got[i] = 1;
+            --left;
+        }
+    }
+    // stops the pump; systems still in the table get their own state back
+    engine_destroy(eh);
     pb_status worst = PB_OK;
-    for (int i = 0; i < n; ++i)
-        if (status[i] != PB_OK) worst = (pb_status)status[i];
+    for (int i = 0; i < n; ++i) {
+        if (!got[i]) {
+            stats[i] = pb_solve_stats{};
+            stats[i].status = rc != PB_OK ? rc : PB_ERR_TIMEOUT;
+            stats[i].seconds = now_s() - t_start;
+        }
+        if (stats[i].status != PB_OK) worst = (pb_status)stats[i].status;
+    }
+    if (rc != PB_OK) return rc;
+    if (timed_out && worst == PB_OK) worst = PB_ERR_TIMEOUT;
     return worst;
 }
 
-#include "engine.cuh"
 
 }  // namespace pbg

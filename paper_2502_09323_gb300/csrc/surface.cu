@@ -1,0 +1,248 @@
+// Re-triangulated molecular surface for the first integral of Eq.
+// energy_ion (Sec. 3.3.2): the surface is rebuilt cell by cell by marching
+// cubes whose vertices are the analytic intersection points r_p of the
+// crossing edges (end nodes in different media), with the analytic normal of
+// the ball surface at each vertex; the integral then takes the vertex rule
+// T_j/3 on every triangle, with phi at the vertices from Eq. phi0 (in the
+// energy kernel).
+//
+// One cell's triangles, without a case table: on each face the crossing
+// edges are joined in pairs (two crossings: one segment; four, the ambiguous
+// face: two segments that each cut off one inside corner, so both cells of a
+// face agree and the surface is closed).  Every crossing edge of the cell
+// lies on two faces, so the segments close into loops; a loop starts at its
+// lowest cell-edge index, first goes to the smaller of that vertex's two
+// neighbours, and is cut into the fan (v0, v_m, v_m+1).
+//
+// k_mc_weight gives every crossing point W = sum of T_j/3 over the triangles
+// of its (up to four) cells that have it as a vertex, visiting the cells in
+// node order and their triangles in fan order, so each sum is formed in one
+// fixed order without atomics.  k_mc_normal finds, through the atom cell
+// list, the ball whose sphere passes closest to the point (smallest
+// | |r_p - c| - R |, ties to the lower atom index) and takes the unit vector
+// from its centre.  This file is compiled without FMA contraction, so every
+// value is reproducible to the bit.
+#include <math.h>
+
+#include "pb_internal.h"
+
+namespace pbg {
+
+namespace {
+
+// cell corners: bit 0 = +x, bit 1 = +y, bit 2 = +z.  Cell edges: 0-3 along
+// x, 4-7 along y, 8-11 along z (corner pairs below).
+__constant__ int8_t c_edge_corner[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                                            {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+// faces: corners in cyclic order, and the cell edge between corner q and q+1
+__constant__ int8_t c_face[6][4] = {{0, 2, 6, 4}, {1, 3, 7, 5}, {0, 1, 5, 4},
+                                    {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 5, 7, 6}};
+__constant__ int8_t c_face_edge[6][4] = {{4, 10, 6, 8}, {5, 11, 7, 9}, {0, 9, 2, 8},
+                                         {1, 11, 3, 10}, {0, 5, 1, 4}, {2, 7, 3, 6}};
+
+// index of edge id in the sorted crossing list (-1 if absent): a binary
+// search inside the id's edge row, [rowstart[r], rowstart[r + 1]) with
+// r = id / nx
+__device__ long long find_edge(const long long *__restrict__ ids, const int *__restrict__ rowstart,
+                               int nx, long long id) {
+    const long long r = id / nx;
+    long long lo = rowstart[r], hi = (long long)rowstart[r + 1] - 1;
+    while (lo <= hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        const long long v = ids[mid];
+        if (v == id) return mid;
+        if (v < id) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// Triangles of cell (i, j, k): crossing-list indices (fan order) and areas.
+__device__ int mc_cell(const GridGeo &g, const uint8_t *__restrict__ inside,
+                       const long long *__restrict__ ids, const int *__restrict__ rowstart,
+                       const double *__restrict__ rp, long long i, long long j, long long k,
+                       long long (*tri)[3], double *area) {
+    long long node[8];
+    int ins = 0;
+    for (int c = 0; c < 8; ++c) {
+        node[c] = ((k + ((c >> 2) & 1)) * g.ny + (j + ((c >> 1) & 1))) * g.nx + (i + (c & 1));
+        if (inside[node[c]]) ins |= 1 << c;
+    }
+    if (ins == 0 || ins == 0xff) return 0;
+    long long vert[12];
+    for (int e = 0; e < 12; ++e) {
+        const int ca = c_edge_corner[e][0], cb = c_edge_corner[e][1];
+        vert[e] = -1;
+        if (((ins >> ca) ^ (ins >> cb)) & 1)
+            vert[e] = find_edge(ids, rowstart, g.nx, (long long)(e / 4) * g.N + node[ca]);
+    }
+    int nbr[12][2], deg[12];
+    for (int e = 0; e < 12; ++e) deg[e] = 0;
+    for (int f = 0; f < 6; ++f) {
+        int cr[4], m = 0;
+        for (int q = 0; q < 4; ++q)
+            if (((ins >> c_face[f][q]) ^ (ins >> c_face[f][(q + 1) & 3])) & 1) cr[m++] = q;
+        int pa[2], pb[2], np = 0;
+        if (m == 2) {
+            pa[0] = c_face_edge[f][cr[0]];
+            pb[0] = c_face_edge[f][cr[1]];
+            np = 1;
+        } else if (m == 4) {
+            // cut off each inside corner (corner q lies between face edges q-1 and q)
+            const int q0 = ((ins >> c_face[f][0]) & 1) ? 0 : 1;
+            pa[0] = c_face_edge[f][(q0 + 3) & 3];
+            pb[0] = c_face_edge[f][q0];
+            pa[1] = c_face_edge[f][(q0 + 1) & 3];
+            pb[1] = c_face_edge[f][(q0 + 2) & 3];
+            np = 2;
+        }
+        for (int p = 0; p < np; ++p) {
+            nbr[pa[p]][deg[pa[p]]++] = pb[p];
+            nbr[pb[p]][deg[pb[p]]++] = pa[p];
+        }
+    }
+    int seen = 0, nt = 0;
+    for (int e0 = 0; e0 < 12; ++e0) {
+        const int ca = c_edge_corner[e0][0], cb = c_edge_corner[e0][1];
+        if (!(((ins >> ca) ^ (ins >> cb)) & 1) || ((seen >> e0) & 1)) continue;
+        int loop[12], len = 0;
+        int prev = e0;
+        int cur = nbr[e0][0] < nbr[e0][1] ? nbr[e0][0] : nbr[e0][1];
+        loop[len++] = e0;
+        seen |= 1 << e0;
+        while (cur != e0 && len < 12) {
+            loop[len++] = cur;
+            seen |= 1 << cur;
+            const int nx = nbr[cur][0] == prev ? nbr[cur][1] : nbr[cur][0];
+            prev = cur;
+            cur = nx;
+        }
+        for (int m = 1; m + 1 < len; ++m) {
+            const long long a = vert[loop[0]], b = vert[loop[m]], c = vert[loop[m + 1]];
+            if (a < 0 || b < 0 || c < 0) continue;
+            const double *p0 = rp + 3 * a, *p1 = rp + 3 * b, *p2 = rp + 3 * c;
+            const double u0 = p1[0] - p0[0], u1 = p1[1] - p0[1], u2 = p1[2] - p0[2];
+            const double v0 = p2[0] - p0[0], v1 = p2[1] - p0[1], v2 = p2[2] - p0[2];
+            const double x = u1 * v2 - u2 * v1;
+            const double y = u2 * v0 - u0 * v2;
+            const double z = u0 * v1 - u1 * v0;
+            tri[nt][0] = a;
+            tri[nt][1] = b;
+            tri[nt][2] = c;
+            area[nt] = 0.5 * sqrt((x * x + y * y) + z * z);
+            ++nt;
+        }
+    }
+    return nt;
+}
+
+__global__ void __launch_bounds__(128)
+k_mc_weight(GridGeo g, const uint8_t *__restrict__ inside, const long long *__restrict__ ids,
+            const int *__restrict__ rowstart, const int8_t *__restrict__ sign,
+            const double *__restrict__ rp, long long ncross, double *__restrict__ W) {
+    const long long s = blockIdx.x * 128ll + threadIdx.x;
+    if (s >= ncross) return;
+    double w = 0.0;
+    if (sign[s] != 0) {
+        const long long id = ids[s];
+        const int d = (int)(id / g.N);
+        const long long a = id - (long long)d * g.N;
+        const long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
+        long long tri[12][3];
+        double area[12];
+        // the (up to) four cells around the edge, in node order
+        for (int v = 0; v < 2; ++v)
+            for (int u = 0; u < 2; ++u) {
+                long long ci = i, cj = j, ck = k;
+                if (d == 0) {
+                    cj = j - 1 + u;
+                    ck = k - 1 + v;
+                } else if (d == 1) {
+                    ci = i - 1 + u;
+                    ck = k - 1 + v;
+                } else {
+                    ci = i - 1 + u;
+                    cj = j - 1 + v;
+                }
+                if (ci < 0 || cj < 0 || ck < 0 || ci > g.nx - 2 || cj > g.ny - 2 || ck > g.nz - 2)
+                    continue;
+                const int nt = mc_cell(g, inside, ids, rowstart, rp, ci, cj, ck, tri, area);
+                for (int t = 0; t < nt; ++t)
+                    if (tri[t][0] == s || tri[t][1] == s || tri[t][2] == s) w += area[t] / 3.0;
+            }
+    }
+    W[s] = w;
+}
+
+__global__ void __launch_bounds__(128)
+k_mc_normal(const double *__restrict__ atoms, long long na, CellList cl,
+            const int8_t *__restrict__ sign, const double *__restrict__ rp, long long ncross,
+            double *__restrict__ nrm) {
+    const long long s = blockIdx.x * 128ll + threadIdx.x;
+    if (s >= ncross) return;
+    double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+    if (sign[s] != 0) {
+        const double p0 = rp[3 * s], p1 = rp[3 * s + 1], p2 = rp[3 * s + 2];
+        const double p[3] = {p0, p1, p2};
+        int cc[3];
+        for (int q = 0; q < 3; ++q) {
+            const double u = floor((p[q] - cl.lo[q]) / cl.cs);
+            cc[q] = (u < -4.0) ? -4 : ((u > (double)cl.dim[q] + 4.0) ? cl.dim[q] + 4 : (int)u);
+        }
+        long long best = -1;
+        double bdev = 0.0, bd = 0.0;
+        for (int cz = cc[2] - 1; cz <= cc[2] + 1; ++cz) {
+            if (cz < 0 || cz >= cl.dim[2]) continue;
+            for (int cy = cc[1] - 1; cy <= cc[1] + 1; ++cy) {
+                if (cy < 0 || cy >= cl.dim[1]) continue;
+                for (int cx = cc[0] - 1; cx <= cc[0] + 1; ++cx) {
+                    if (cx < 0 || cx >= cl.dim[0]) continue;
+                    const int cid = (cz * cl.dim[1] + cy) * cl.dim[0] + cx;
+                    for (int q = cl.start[cid]; q < cl.start[cid + 1]; ++q) {
+                        const long long at = cl.atom[q];
+                        const double dx = p0 - atoms[at], dy = p1 - atoms[na + at],
+                                     dz = p2 - atoms[2 * na + at];
+                        const double dd = sqrt((dx * dx + dy * dy) + dz * dz);
+                        const double dev = fabs(dd - atoms[3 * na + at]);
+                        if (best < 0 || dev < bdev || (dev == bdev && at < best)) {
+                            best = at;
+                            bdev = dev;
+                            bd = dd;
+                        }
+                    }
+                }
+            }
+        }
+        if (best >= 0) {
+            o0 = (p0 - atoms[best]) / bd;
+            o1 = (p1 - atoms[na + best]) / bd;
+            o2 = (p2 - atoms[2 * na + best]) / bd;
+        }
+    }
+    nrm[3 * s] = o0;
+    nrm[3 * s + 1] = o1;
+    nrm[3 * s + 2] = o2;
+}
+
+}  // namespace
+
+// Vertex weights and normals of the re-triangulated surface (uniform grids).
+pb_status mc_surface(pb_system *sys, cudaStream_t s) {
+    pb_grid *g = sys->g;
+    const long long nc = g->ncross;
+    if (!sys->mc_w) {
+        sys->mc_w = (double *)dalloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1), s);
+        sys->mc_n = (double *)dalloc(sizeof(double) * 3 * (size_t)(nc > 0 ? nc : 1), s);
+        if (!sys->mc_w || !sys->mc_n) return PB_ERR_OOM;
+    }
+    if (nc == 0) return PB_OK;
+    k_mc_weight<<<cdiv(nc, 128), 128, 0, s>>>(g->geo, g->inside, g->cid, g->rowstart, g->csign,
+                                              g->crp, nc, sys->mc_w);
+    PB_LAUNCH_CHECK();
+    k_mc_normal<<<cdiv(nc, 128), 128, 0, s>>>(g->atoms, g->na, g->cells, g->csign, g->crp, nc,
+                                              sys->mc_n);
+    PB_LAUNCH_CHECK();
+    return PB_OK;
+}
+
+}  // namespace pbg

@@ -114,3 +114,15 @@ def test_device_wait_limit_expires_then_solves(pb):
     sts = pb.pb_solve_batch([a, b], opts)
     for s, p in zip((a, b), phi_ref):
         assert np.array_equal(pb.pb_get_phi(s), p)
+
+
+def test_batch_time_budget_runs_out_then_solves(pb):
+    """A batch whose time budget runs out reports PB_ERR_TIMEOUT for the
+    systems it did not finish, hands every system back, and the same systems
+    then solve normally."""
+    a, b = _system(pb, 65), _system(pb, 97)
+    sts = pb.pb_solve_batch([a, b], pb.SolveOpts(precision=pb.MIXED, rtol=1e-12,
+                                                 time_budget_s=1e-5), check=False)
+    assert sts[0]["rc"] == -5 and any(s["status"] == -5 for s in sts)
+    sts = pb.pb_solve_batch([a, b], pb.SolveOpts(precision=pb.MIXED, rtol=1e-8))
+    assert all(s["status"] == 0 and s["true_rel_res"] <= 1e-8 for s in sts)

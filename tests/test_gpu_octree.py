@@ -46,6 +46,12 @@ CASES = {
     "mid250": (lambda: pb_inputs.globular_molecule(250, seed=77),
                dict(h_fine=0.25, h_bulk=1.0, refine_dist=3.0, fill=1.5),
                dict(bc=2)),
+    # de-refined domain (Sec. 3.4): tight box at 0.5 A, 2 A far field,
+    # perfil about 15 %, homogeneous Dirichlet values
+    "deref": (lambda: pb_inputs.globular_molecule(20, seed=41),
+              dict(h_fine=0.25, h_bulk=2.0, refine_dist=3.0, fill=1 / 0.15, h_tight=0.5,
+                   tight_fill=1.1),
+              dict(bc=0)),
 }
 
 
@@ -55,6 +61,8 @@ def case(request, pb, O):
     atoms = atoms_fn()
     spec = pb.OctreeSpec(**skw)
     okw = dict(h_fine=skw["h_fine"], h_bulk=skw["h_bulk"], refine_dist=skw["refine_dist"])
+    if skw.get("h_tight"):
+        okw.update(h_tight=skw["h_tight"], tight_fill=skw["tight_fill"])
     if skw.get("n0", 0) > 0:
         tree = O.build(atoms, origin=np.array(skw["origin"]), n0=skw["n0"], **okw)
     else:
@@ -196,8 +204,23 @@ def test_octree_argument_errors(pb):
     assert ei.value.code == -1
     with pytest.raises(pb.PBError):
         pb.pb_build_grid(pb.OctreeSpec(h_fine=0.5, h_bulk=1.5, refine_dist=3.0), atoms)
-    g = pb.pb_build_grid(pb.OctreeSpec(h_fine=0.5, h_bulk=1.0, refine_dist=3.0, fill=3.0), atoms)
-    s = pb.pb_assemble_coeffs(g, pb.Params())
-    with pytest.raises(pb.PBError) as ei:
-        pb.pb_solve_batch([s], pb.SolveOpts())
-    assert ei.value.code == -7
+
+def test_octree_in_a_batch_equals_alone(pb):
+    """pb_solve_batch takes octree systems beside uniform ones: each result
+    is the same bits as its own pb_solve."""
+    opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-9)
+
+    def systems():
+        a = pb_inputs.globular_molecule(60, seed=91)
+        go = pb.pb_build_grid(pb.OctreeSpec(h_fine=0.5, h_bulk=1.0, refine_dist=3.0, fill=1.5), a)
+        gu = pb.pb_build_grid(pb.GridSpec(n=(49, 49, 49), fill=1.6), a)
+        return [pb.pb_assemble_coeffs(go, pb.Params()), pb.pb_assemble_coeffs(gu, pb.Params())]
+
+    alone = systems()
+    ref = [(pb.pb_solve(s, opts), pb.pb_get_phi(s)) for s in alone]
+    mix = systems()
+    stats = pb.pb_solve_batch(mix, opts)
+    for s, st, (st_ref, phi) in zip(mix, stats, ref):
+        assert st["status"] == 0 and st["true_rel_res"] <= 1e-9
+        assert st["iters_inner"] == st_ref["iters_inner"]
+        assert np.array_equal(pb.pb_get_phi(s), phi)

@@ -163,9 +163,28 @@ def test_solve_residual_and_energy(pb, case, prec, orc):
     assert rel <= 1e-8
     e = pb.pb_energy(s)
     er = ref["energy"]
-    for k in ("e_pol", "e_ion_flux", "e_ion_surf", "e_coul", "e_total"):
+    for k in ("e_pol", "e_ion_flux", "e_ion_surf", "e_coul", "e_total", "e_ion_mc"):
         assert abs(e[k] - er[k]) <= 1e-6 * max(abs(er[k]), 1e-3 * abs(er["e_pol"])), k
     assert abs(e["flux_charge"] - case["atoms"][:, 4].sum()) < 1e-6 * np.abs(case["atoms"][:, 4]).sum()
+
+
+def test_retriangulated_surface(pb, case, orc):
+    """Marching-cubes vertex weights (T_j/3 sums) and analytic normals bit
+    for bit; Psi along the normals within the compensated FP32 bound."""
+    s, ref, atoms = case["s"], case["ref"], case["atoms"]
+    pb.pb_coulomb_terms(s, pb.CT_SURFACE)
+    cr = ref["cross"]
+    W = pb.pb_get_array(s, "mc_weight")
+    nrm = pb.pb_get_array(s, "mc_normal")
+    assert np.array_equal(W, ref["mc"]["W"])
+    assert np.array_equal(nrm, ref["mc"]["normals"])
+    flux = cr["sign"] != 0
+    psi = pb.pb_get_array(s, "psi_n")
+    psi_ref = orc.coulomb_psi_n(cr["rp"][flux], nrm[flux], atoms)
+    r = np.linalg.norm(cr["rp"][flux][:, None, :] - atoms[None, :, :3], axis=2)
+    absq = np.abs(atoms[:, 4])[None, :]
+    assert np.max(np.abs(psi[flux] - psi_ref) / (absq / r ** 2).sum(1)) <= 2e-6
+    assert not psi[~flux].any()
 
 
 def test_surface_coulomb_terms(pb, case, orc):
