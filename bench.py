@@ -797,13 +797,17 @@ def run_ours(args, wl):
         kt[name] = a.elapsed_time(b) / 1e3 / reps
     bytes_u = dof * ALG_BYTES_U32
     achieved = bytes_u / kt["update"] / 1e9
-    traffic = None
+    # DRAM bytes of one launch from the stored ncu capture of this kernel on
+    # this workload (a profiler run is not a bench run); null without it
+    traffic, traffic_source = None, None
     tpath = os.path.join(ROOT, "profiles", "stencil_update_fp32_globular257.json")
-    if os.path.exists(tpath):
+    if os.path.exists(tpath) and wl["n"] == 257:
         with open(tpath) as fh:
-            traffic = json.load(fh).get("dram_bytes_per_launch")
+            rec = json.load(fh)
+        traffic = rec.get("dram_bytes_per_launch")
+        traffic_source = rec.get("source")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
                 "kernel": ("k_stencil_tma<MODE_U> (FP32 PCG update, TMA-staged, persistent)"
                            if stats[-1]["kc"] >= 1000 else
                            "k_stencil<float,CoefC32,MODE_U> (FP32 PCG update)"),

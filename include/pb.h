@@ -378,6 +378,24 @@ pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int
  * autotuner's choice (which times the candidates on first use of a shape). */
 pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_t z_chunk);
 
+/* pb_solve_split -- the mixed-precision solve of pb_solve (uniform grids) on
+ * `ranks` z-slabs (1 .. min(64, nz - 2)): the multi-GPU decomposition of one
+ * system (Sec. 4 solves on distributed memory).  Each rank holds its owned
+ * planes plus one halo plane on each side in its own buffers; before the
+ * direction kernels the z halos, before the update kernels the new p halos,
+ * and before every FP64 residual the phi halos are copied from the
+ * neighbours into each receiver's memory (cudaMemcpyPeerAsync); each
+ * kernel round's partial dot products are added in rank order and the CG
+ * update is written to every rank, so all ranks take the same decisions.
+ * In this build every rank lives on the system's device.  ranks = 1 gives
+ * pb_solve's result bit for bit (same z-chunk); more ranks change only the
+ * order of the dot-product sums.  phi is gathered back into s (pb_energy
+ * works as after pb_solve).  Errors: PB_ERR_ARG for a bad rank count or a
+ * precision other than PB_MIXED, PB_ERR_UNIMPL for octree systems, and the
+ * statuses of pb_solve. */
+pb_status pb_solve_split(pb_system *s, int32_t ranks, const pb_solve_opts *opts, void *stream,
+                         pb_solve_stats *stats);
+
 /* pb_set_wait_limit -- failure-injection hook for tests: the number of polls
  * after which a ring-slot wait of the FP32 PCG kernels (one-system, batched
  * and served launches) gives up; polls < 0 restores the default (2^20).  With

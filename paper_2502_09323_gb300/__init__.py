@@ -28,7 +28,7 @@ __all__ = [
     "GridSpec", "OctreeSpec", "Params", "SolveOpts", "Grid", "System",
     "pb_build_grid", "pb_assemble_coeffs", "pb_coulomb_terms", "pb_solve", "pb_energy",
     "pb_get_array", "pb_get_phi", "pb_apply", "pb_solve_batch", "pb_last_error",
-    "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning", "pb_set_wait_limit",
+    "pb_profile_kernels", "pb_kernel_launches", "pb_set_tuning", "pb_set_wait_limit", "pb_solve_split",
     "solve_molecule", "library_path", "loaded", "PBError", "Engine",
 ]
 
@@ -436,6 +436,19 @@ def pb_profile_kernels(system: System, precision: int, which: int, reps: int, st
 
 def pb_set_tuning(system: System, precision: int, variant: int, z_chunk: int) -> None:
     N.check(N.lib().pb_set_tuning(system.handle, int(precision), int(variant), int(z_chunk)))
+
+
+def pb_solve_split(system: System, ranks: int, opts: SolveOpts, stream=None, check=True) -> dict:
+    """The mixed-precision solve on ``ranks`` z-slabs with halo exchanges and
+    rank-ordered reductions; statistics as from :func:`pb_solve`."""
+    stats = N.SolveStatsC()
+    rc = N.lib().pb_solve_split(system.handle, int(ranks), C.byref(opts.c()), _stream(stream),
+                                C.byref(stats))
+    if check:
+        N.check(rc)
+    d = N.struct_dict(stats)
+    d["rc"] = rc
+    return d
 
 
 def pb_set_wait_limit(polls: int) -> None:

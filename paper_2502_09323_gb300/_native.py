@@ -91,6 +91,7 @@ SIGNATURES = {
     "pb_kernel_launches": (C.c_int64, []),
     "pb_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "pb_set_wait_limit": (C.c_int, [C.c_int64]),
+    "pb_solve_split": (C.c_int, [P, C.c_int32, P, P, P]),
     "pb_apply_dot_noalloc": (C.c_int, [P, P, P, P, P]),
     "pb_engine_create": (C.c_int, [C.c_int32, C.c_int32, P, P]),
     "pb_engine_submit": (C.c_int, [P, P, P, P]),

@@ -719,6 +719,30 @@ pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_
     return set_tuning(s, precision, variant, z_chunk);
 }
 
+pb_status pb_solve_split(pb_system *s, int32_t ranks, const pb_solve_opts *opts, void *stream,
+                         pb_solve_stats *stats) {
+    set_error("");
+    if (!s) {
+        set_error("pb_solve_split: NULL system");
+        return PB_ERR_ARG;
+    }
+    pb_status rc = check_opts(opts);
+    if (rc != PB_OK) return rc;
+    if (opts->precision != PB_MIXED) {
+        set_error("pb_solve_split: the split solve runs the mixed-precision solver");
+        return PB_ERR_ARG;
+    }
+    if (s->g->is_oct) {
+        set_error("pb_solve_split: octree systems are solved by pb_solve");
+        return PB_ERR_UNIMPL;
+    }
+    DeviceGuard dg(s->g->device);
+    rc = solve_split(s, ranks, opts, (cudaStream_t)stream, stats);
+    if (rc == PB_ERR_NOCONV) set_error("solver stopped before reaching rtol");
+    if (rc == PB_ERR_TIMEOUT && !g_err[0]) set_error("solver exceeded its time budget");
+    return rc;
+}
+
 pb_status pb_set_wait_limit(int64_t polls) {
     set_error("");
     return set_wait_limit((long long)polls);

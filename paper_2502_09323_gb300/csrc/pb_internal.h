@@ -155,7 +155,9 @@ struct CgState {
     unsigned int counter;  // last-block counter of the reductions
     int profile;     // 1 = timing run: never stop
     int cur;         // FP32 TMA kernels: which of pa/pb holds p_old (flips per iteration)
-    int pad;
+    int split;       // 1: one slab of a split solve (the launch stores its totals in
+                     // part0/part1; the CG update runs after the rank-ordered sum)
+    double part0, part1;
 };
 
 struct EnergyAcc {
@@ -232,6 +234,8 @@ void free_tma_state(pb_system *sys);
 pb_status set_tuning(pb_system *sys, int precision, int variant, int kc);
 pb_status set_wait_limit(long long polls);
 pb_status solve_batch(pb_system *const *systems, int n, const pb_solve_opts *o, cudaStream_t s,
+                      pb_solve_stats *stats);
+pb_status solve_split(pb_system *sys, int ranks, const pb_solve_opts *o, cudaStream_t s,
                       pb_solve_stats *stats);
 pb_status engine_create(int device, int capacity, const pb_solve_opts *o, pb_engine **out);
 pb_status engine_submit(pb_engine *e, pb_system *sys, cudaStream_t s, long long *ticket);

@@ -511,7 +511,8 @@ __global__ void __launch_bounds__(256)
 k_residual(const double *__restrict__ phi, const double *__restrict__ f,
            const double *__restrict__ Wx, const double *__restrict__ Wy,
            const double *__restrict__ Wz, const double *__restrict__ diag, GridGeo g, PadGeo pg,
-           TZ *__restrict__ zout, CgState *st, double *partials, double *__restrict__ rout) {
+           TZ *__restrict__ zout, CgState *st, double *partials, double *__restrict__ rout,
+           int kofs = 0, int nzg = 0) {
     __shared__ double sred[8];
     __shared__ TZ sblk[2][8];
     const long long stride = (long long)gridDim.x * 256;
@@ -538,8 +539,9 @@ k_residual(const double *__restrict__ phi, const double *__restrict__ f,
         if (i < g.nx - 2) sum -= Wx[a] * phi[a + 1];
         if (j > 1) sum -= Wy[a - sy] * phi[a - sy];
         if (j < g.ny - 2) sum -= Wy[a] * phi[a + sy];
-        if (k > 1) sum -= Wz[a - sz] * phi[a - sz];
-        if (k < g.nz - 2) sum -= Wz[a] * phi[a + sz];
+        // a slab of a split solve: local plane k is global plane k + kofs
+        if (k + kofs > 1) sum -= Wz[a - sz] * phi[a - sz];
+        if (k + kofs < (nzg > 0 ? nzg : g.nz) - 2) sum -= Wz[a] * phi[a + sz];
         double r = f[a] - sum;
         TZ z, rt;
         if (sizeof(TZ) == 4) {
@@ -1588,6 +1590,7 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
 namespace pbg {
 
 #include "engine.cuh"
+#include "split.cuh"
 
 // Batched mixed-precision solve through the continuous-batching engine: every
 // system takes a slot of one launch table, whose PCG iterations run as

@@ -749,6 +749,12 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         constexpr int BIGSYS = 512;
         __shared__ double s_red[2][NTHREADS / 32];
         auto finish = [&](CgState *st, double t0, double t1) {
+            if (st->split) {
+                // one slab of a split solve: its totals only
+                st->part0 = t0;
+                st->part1 = t1;
+                return;
+            }
             if (MODE == MODE_P) {
                 st->sigma = t0;
                 if (st->status == 3) {
