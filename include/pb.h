@@ -173,8 +173,9 @@ typedef struct {
  *               re-triangulated by marching cubes through the intersection
  *               points r_e, T_e = sum of T_j/3 over the triangles with vertex
  *               r_e, Psi^n_e with the analytic ball normal at r_e, phi(r_e)
- *               from Eq. phi0 (uniform grids; 0 on octree grids).  The paper's
- *               E_ion is e_ion_mc + e_ion_flux.
+ *               from Eq. phi0 (on octree grids, the surface of the finest
+ *               lattice, where every listed edge lies).  The paper's E_ion
+ *               is e_ion_mc + e_ion_flux.
  * F_e = W_e (phi_in - phi_out) over flux edges (endpoints in different
  * media), Phi_e = sum_i q_i/|r_e - r_i|, Psi_e = sum_i q_i (r_e - r_i).n_e /
  * |r_e - r_i|^3, n_e the unit edge direction from the inside endpoint. */
@@ -224,13 +225,14 @@ enum {
     PB_ARR_OCT_KIND,     /* uint8  [N] octree: 0 unknown with a 7-point row, 1
                             boundary, 2 hanging, 3 unknown next to a level
                             change (explicit row)                           */
-    PB_ARR_MC_WEIGHT,    /* double [n_cross] uniform grids: T_e, the sum of T_j/3
-                            over the marching-cubes triangles with vertex r_e
-                            (0 on edges whose endpoints share a medium)       */
-    PB_ARR_MC_NORMAL,    /* double [3*n_cross] uniform grids: analytic outward
-                            unit normal of the ball surface at r_e            */
-    PB_ARR_PSI_N,        /* double [n_cross] uniform grids: Psi along that
-                            normal                                            */
+    PB_ARR_MC_WEIGHT,    /* double [n_cross] T_e, the sum of T_j/3 over the
+                            marching-cubes triangles with vertex r_e (0 on
+                            edges whose endpoints share a medium); crossing
+                            order of the grid (uniform or octree)             */
+    PB_ARR_MC_NORMAL,    /* double [3*n_cross] analytic outward unit normal of
+                            the ball surface at r_e                           */
+    PB_ARR_PSI_N,        /* double [n_cross] Psi along that normal (a system
+                            after pb_coulomb_terms with the surface terms)    */
     PB_ARR_COUNT
 };
 

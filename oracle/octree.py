@@ -388,9 +388,14 @@ def crossing_edges(tree: Octree, op: dict, atoms) -> dict:
     in the all-finest region, so they are the listed edges of the uniform
     grid at h_fine spanning the domain, with the same alpha, r_p and sign.
     Adds the octree position indices of their ends and their slot-based id
-    d * (512 nb) + slot(a)."""
+    d * (512 nb) + slot(a).  The re-triangulated surface of Sec. 3.3.2 is
+    that of the same uniform grid: its vertex weights ("mc_w") and analytic
+    normals ("mc_n") come along with each edge."""
     g = _virtual_grid(tree, tree.Lmax)
-    cr = U.crossing_edges(g, atoms, U.classify(g, atoms))
+    inside_g = U.classify(g, atoms)
+    cr = U.crossing_edges(g, atoms, inside_g)
+    cr["mc_w"] = U.mc_weights(g, inside_g, cr)
+    cr["mc_n"] = U.mc_normals(cr, atoms)
     n = int(g.n[0])
     N = n ** 3
     d = (cr["ids"] // N).astype(np.int64)
@@ -538,7 +543,8 @@ def energy(tree: Octree, op: dict, cross: dict, phi_pos: np.ndarray, atoms, lB, 
            eps_out) -> dict:
     """Energy terms of Sec. 3.3 from phi at all positions, over the flux
     edges (ends in different media) of the crossing list: Eq. polen, Eq.
-    energy_ion (first integral on staircase faces with Eq. phi0)."""
+    energy_ion (first integral on staircase faces with Eq. phi0, and on the
+    re-triangulated surface of Sec. 3.3.2 as "e_ion_mc")."""
     e = op["edges"]
     flux = np.nonzero(cross["sign"] != 0)[0]
     a, b, d = cross["a"][flux], cross["b"][flux], cross["d"][flux]
@@ -559,13 +565,17 @@ def energy(tree: Octree, op: dict, cross: dict, phi_pos: np.ndarray, atoms, lB, 
     h = tree.h_fine
     S = float(np.sum(F * Phi))
     I = float(np.sum(phip * (h * h) * Psi))
+    W = cross["mc_w"][flux]
+    psin = U.coulomb_psi_n(rp, cross["mc_n"][flux], atoms)
+    Imc = float(np.sum(W * phip * psin))
     e_coul = U.ecoul(atoms, lB, eps_in)
     e_pol = 0.5 * (1.0 / eps_out - 1.0 / eps_in) * S / (4.0 * math.pi)
     e_ion_flux = -0.5 * (1.0 / eps_out) * S / (4.0 * math.pi)
     e_ion_surf = 0.5 * I / (4.0 * math.pi)
     return {"e_coul": e_coul, "e_pol": e_pol, "e_ion_surf": e_ion_surf,
             "e_ion_flux": e_ion_flux, "e_total": e_coul + e_pol + e_ion_surf + e_ion_flux,
-            "flux_charge": float(np.sum(F)) / (4.0 * math.pi * lB)}
+            "flux_charge": float(np.sum(F)) / (4.0 * math.pi * lB),
+            "e_ion_mc": 0.5 * Imc / (4.0 * math.pi)}
 
 
 def solve_problem(atoms, tree: Octree, eps_in=2.0, eps_out=80.0, ionic_strength_M=0.145,

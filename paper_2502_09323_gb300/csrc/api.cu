@@ -148,6 +148,8 @@ void pb_grid_free(pb_grid *g) {
     dfree(g->crp, s);
     dfree(g->csign, s);
     dfree(g->rowstart, s);
+    dfree(g->mc_w, s);
+    dfree(g->mc_n, s);
     dfree(g->d_info, s);
     if (g->is_oct) oct_grid_free(g, s);
     cudaStreamSynchronize(s);
@@ -295,8 +297,7 @@ void pb_system_free(pb_system *s) {
     void *ptrs[] = {s->W[0], s->W[1], s->W[2], s->diag, s->rhs, s->bc, s->phi, s->code, s->w32[0], s->w32[1], s->w32[2],
                     s->z32, s->pa32, s->pb32, s->d32, s->z64, s->pa64, s->pb64, s->x64,
                     s->r64, s->q64, s->op64[0], s->op64[1], s->op64[2], s->op64[3], s->op64[4],
-                    s->partials, s->queue, s->st, s->Phi, s->Psi, s->eacc, s->mc_w, s->mc_n,
-                    s->PsiN};
+                    s->partials, s->queue, s->st, s->Phi, s->Psi, s->eacc, s->PsiN};
     for (void *p : ptrs) dfree(p, st);
     oct_system_free(s, st);
     cudaStreamSynchronize(st);
@@ -532,17 +533,21 @@ pb_status pb_get_array(const pb_grid *g, const pb_system *s, int32_t which, void
             default: break;
         }
     }
-    if (which >= PB_ARR_MC_WEIGHT && which <= PB_ARR_PSI_N) {
-        if (!s || g->is_oct) {
-            set_error("array %d needs a system on a uniform grid", which);
+    if (which == PB_ARR_MC_WEIGHT || which == PB_ARR_MC_NORMAL) {
+        src = which == PB_ARR_MC_WEIGHT ? g->mc_w : g->mc_n;
+        need = (which == PB_ARR_MC_NORMAL ? 24 : 8) * nc;
+    }
+    if (which == PB_ARR_PSI_N) {
+        if (!s) {
+            set_error("array %d needs a system", which);
             return PB_ERR_ARG;
         }
-        if (!s->have_surface || !s->mc_w) {
+        if (!s->have_surface || !s->PsiN) {
             set_error("surface Coulomb terms not computed");
             return PB_ERR_STATE;
         }
-        src = which == PB_ARR_MC_WEIGHT ? s->mc_w : (which == PB_ARR_MC_NORMAL ? s->mc_n : s->PsiN);
-        need = (which == PB_ARR_MC_NORMAL ? 24 : 8) * nc;
+        src = s->PsiN;
+        need = 8 * nc;
     }
     if (bytes < need) {
         set_error("destination too small: %zu < %zu bytes", bytes, need);

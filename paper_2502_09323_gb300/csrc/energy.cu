@@ -124,7 +124,7 @@ pb_status energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out) {
     PB_CUDA_TRY(cudaMemsetAsync(&sys->eacc->counter, 0, sizeof(unsigned), s));
     k_energy<<<nb, EN_THREADS, 0, s>>>(g->cid, g->calpha, g->csign, g->ncross, sys->W[0], sys->W[1],
                                        sys->W[2], sys->phi, sys->Phi, sys->Psi,
-                                       g->is_oct ? nullptr : sys->mc_w, sys->PsiN, g->geo,
+                                       g->mc_w, sys->PsiN, g->geo,
                                        sys->p.eps_in, sys->p.eps_out, sys->lB, partials, sys->eacc);
     PB_LAUNCH_CHECK();
     PB_CUDA_TRY(cudaMemcpyAsync(sys->h_energy, &sys->eacc->out, sizeof(pb_energy_terms),

@@ -808,7 +808,9 @@ pb_status grid_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
     }
     g->nflux = (long long)hinfo.nflux;
     g->ninside = (long long)hinfo.ninside;
-    return PB_OK;
+    // the surface re-triangulated through the crossing points (first
+    // integral of Eq. energy_ion, Sec. 3.3.2): vertex weights and normals
+    return mc_surface(g, s);
 }
 
 }  // namespace pbg

@@ -409,22 +409,15 @@ pb_status nbody_surface(pb_system *sys, cudaStream_t s) {
     if (st != PB_OK) return st;
     TargetDesc T = make_desc(sys, TK_SURFACE);
     T.count = g->ncross;
-    if (g->is_oct) {
-        k_nbody<true, false><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
-            T, hi, lo, g->na, 0.f, 1.0, sys->Phi, sys->Psi);
-        PB_LAUNCH_CHECK();
-    } else {
-        // the re-triangulated surface (vertex weights, analytic normals);
-        // Psi along those normals comes from the same pairs as Phi and Psi
-        // (first integral of Eq. energy_ion, Sec. 3.3.2)
-        if (!sys->PsiN) sys->PsiN = (double *)dalloc(sizeof(double) * nc, s);
-        if (!sys->PsiN) return PB_ERR_OOM;
-        if ((st = mc_surface(sys, s)) != PB_OK) return st;
-        T.nrm2 = sys->mc_n;
-        k_nbody<true, false, true><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
-            T, hi, lo, g->na, 0.f, 1.0, sys->Phi, sys->Psi, sys->PsiN);
-        PB_LAUNCH_CHECK();
-    }
+    // Psi along the re-triangulated surface's analytic normals (first
+    // integral of Eq. energy_ion, Sec. 3.3.2) comes from the same pairs as
+    // Phi and Psi
+    if (!sys->PsiN) sys->PsiN = (double *)dalloc(sizeof(double) * nc, s);
+    if (!sys->PsiN) return PB_ERR_OOM;
+    T.nrm2 = g->mc_n;
+    k_nbody<true, false, true><<<cdiv(T.count, NB_THREADS * NB_TPT), NB_THREADS, 0, s>>>(
+        T, hi, lo, g->na, 0.f, 1.0, sys->Phi, sys->Psi, sys->PsiN);
+    PB_LAUNCH_CHECK();
     dfree(hi, s);
     dfree(lo, s);
     return PB_OK;

@@ -1500,9 +1500,10 @@ k_oct_energy(const long long *__restrict__ ids, const long long *__restrict__ sl
              const double *__restrict__ alpha, const int8_t *__restrict__ sign, long long ncross,
              long long N, const double *__restrict__ W0, const double *__restrict__ W1,
              const double *__restrict__ W2, const double *__restrict__ phi,
-             const double *__restrict__ Phi, const double *__restrict__ Psi, double h,
+             const double *__restrict__ Phi, const double *__restrict__ Psi,
+             const double *__restrict__ Tw, const double *__restrict__ PsiN, double h,
              double eps_in, double eps_out, double lB, double *partials, EnergyAcc *acc) {
-    double S = 0.0, I = 0.0, F = 0.0;
+    double S = 0.0, I = 0.0, F = 0.0, Im = 0.0;
     for (long long s = blockIdx.x * (long long)EN_T + threadIdx.x; s < ncross;
          s += (long long)gridDim.x * EN_T) {
         const int sg = sign[s];
@@ -1518,14 +1519,16 @@ k_oct_energy(const long long *__restrict__ ids, const long long *__restrict__ sl
         S += Fe * Phi[s];
         I += phip * (h * h) * Psi[s];
         F += Fe;
+        Im += Tw[s] * phip * PsiN[s];
     }
-    double mine[3] = {S, I, F}, tot[3];
-    if (olast_total<EN_T, 3>(&acc->counter, partials, mine, tot)) {
+    double mine[4] = {S, I, F, Im}, tot[4];
+    if (olast_total<EN_T, 4>(&acc->counter, partials, mine, tot)) {
         if (threadIdx.x == 0) {
             const double fourpi = 4.0 * M_PI;
             acc->S = tot[0];
             acc->I = tot[1];
             acc->F = tot[2];
+            acc->Imc = tot[3];
             pb_energy_terms o{};
             o.e_coul = (lB / eps_in) * 0.5 * acc->ecoul_sum;
             o.e_pol = 0.5 * (1.0 / eps_out - 1.0 / eps_in) * tot[0] / fourpi;
@@ -1533,7 +1536,7 @@ k_oct_energy(const long long *__restrict__ ids, const long long *__restrict__ sl
             o.e_ion_surf = 0.5 * tot[1] / fourpi;
             o.e_total = o.e_coul + o.e_pol + o.e_ion_surf + o.e_ion_flux;
             o.flux_charge = tot[2] / (fourpi * lB);
-            o.e_ion_mc = 0.0;  // the re-triangulated surface is built on uniform grids
+            o.e_ion_mc = 0.5 * tot[3] / fourpi;
             acc->out = o;
             acc->counter = 0;
         }
@@ -1796,6 +1799,18 @@ pb_status oct_build(pb_grid *g, const pb_grid_spec *spec, cudaStream_t s) {
         k_gather<long long><<<cdiv(ncr, OT), OT, 0, s>>>(sb, perm2, ncr, 1, g->cslot_b);
         PB_LAUNCH_CHECK();
         note_launch(4);
+        // the re-triangulated surface of the finest lattice, in the new order
+        double *mw2 = (double *)dalloc(sizeof(double) * ncr, s);
+        double *mn2 = (double *)dalloc(sizeof(double) * 3 * ncr, s);
+        if (!mw2 || !mn2) return PB_ERR_OOM;
+        k_gather<double><<<cdiv(ncr, OT), OT, 0, s>>>(g->mc_w, perm2, ncr, 1, mw2);
+        k_gather<double><<<cdiv(3 * ncr, OT), OT, 0, s>>>(g->mc_n, perm2, ncr, 3, mn2);
+        PB_LAUNCH_CHECK();
+        note_launch(1);
+        dfree(g->mc_w, s);
+        dfree(g->mc_n, s);
+        g->mc_w = mw2;
+        g->mc_n = mn2;
         dfree(tmp, s);
         dfree(oid, s);
         dfree(oid2, s);
@@ -2382,11 +2397,12 @@ pb_status oct_energy(pb_system *sys, cudaStream_t s, pb_energy_terms *out) {
     pb_grid *g = sys->g;
     const int nb = (int)std::min<long long>(cdiv(g->ncross > 0 ? g->ncross : 1, EN_T),
                                             (long long)num_sms() * 8);
-    double *partials = (double *)dalloc(sizeof(double) * 3 * nb, s);
+    double *partials = (double *)dalloc(sizeof(double) * 4 * nb, s);
     if (!partials) return PB_ERR_OOM;
     PB_CUDA_TRY(cudaMemsetAsync(&sys->eacc->counter, 0, sizeof(unsigned), s));
     k_oct_energy<<<nb, EN_T, 0, s>>>(g->cid, g->cslot_b, g->calpha, g->csign, g->ncross, g->ot.N,
                                      sys->W[0], sys->W[1], sys->W[2], sys->phi, sys->Phi, sys->Psi,
+                                     g->mc_w, sys->PsiN,
                                      g->ot.hf, sys->p.eps_in, sys->p.eps_out, sys->lB, partials,
                                      sys->eacc);
     PB_LAUNCH_CHECK();

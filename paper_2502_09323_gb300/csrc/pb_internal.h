@@ -134,6 +134,8 @@ struct pb_grid {
     pbg::OctDev ot;
     pbg::GridGeo vgeo;    // octree: the uniform lattice at the finest spacing
     long long *cslot_b;   // octree: slot of the +d end of each listed edge
+    double *mc_w;         // [ncross] re-triangulated surface: vertex weight (sum of T_j/3)
+    double *mc_n;         // [3 ncross] analytic outward unit normal at each crossing point
 };
 
 namespace pbg {
@@ -195,9 +197,7 @@ struct pb_system {
     pbg::CgState *st;
     pbg::CgState *h_st; // pinned host mirror
     double *Phi, *Psi;  // [ncross]
-    // uniform grids: re-triangulated surface (vertex weights T_j/3, analytic
-    // unit normals) and Psi along those normals, [ncross] / [3 ncross]
-    double *mc_w, *mc_n, *PsiN;
+    double *PsiN;       // [ncross] Psi along the grid's analytic normals (mc_n)
     pbg::EnergyAcc *eacc;
     pb_energy_terms *h_energy;  // pinned
     int solved, have_surface, have_pairs;
@@ -223,7 +223,7 @@ pb_status nbody_surface(pb_system *sys, cudaStream_t s);
 pb_status nbody_pairs(pb_system *sys, cudaStream_t s);
 
 // ------------------------------------------------------------ surface.cu --
-pb_status mc_surface(pb_system *sys, cudaStream_t s);
+pb_status mc_surface(pb_grid *g, cudaStream_t s);
 
 // -------------------------------------------------------------- solve.cu --
 pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve_stats *st);

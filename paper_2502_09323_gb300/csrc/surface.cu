@@ -226,21 +226,19 @@ k_mc_normal(const double *__restrict__ atoms, long long na, CellList cl,
 
 }  // namespace
 
-// Vertex weights and normals of the re-triangulated surface (uniform grids).
-pb_status mc_surface(pb_system *sys, cudaStream_t s) {
-    pb_grid *g = sys->g;
+// Vertex weights and normals of the re-triangulated surface, from the
+// uniform grid pass (the grid itself, or an octree's finest lattice).
+pb_status mc_surface(pb_grid *g, cudaStream_t s) {
     const long long nc = g->ncross;
-    if (!sys->mc_w) {
-        sys->mc_w = (double *)dalloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1), s);
-        sys->mc_n = (double *)dalloc(sizeof(double) * 3 * (size_t)(nc > 0 ? nc : 1), s);
-        if (!sys->mc_w || !sys->mc_n) return PB_ERR_OOM;
-    }
+    g->mc_w = (double *)dalloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1), s);
+    g->mc_n = (double *)dalloc(sizeof(double) * 3 * (size_t)(nc > 0 ? nc : 1), s);
+    if (!g->mc_w || !g->mc_n) return PB_ERR_OOM;
     if (nc == 0) return PB_OK;
     k_mc_weight<<<cdiv(nc, 128), 128, 0, s>>>(g->geo, g->inside, g->cid, g->rowstart, g->csign,
-                                              g->crp, nc, sys->mc_w);
+                                              g->crp, nc, g->mc_w);
     PB_LAUNCH_CHECK();
     k_mc_normal<<<cdiv(nc, 128), 128, 0, s>>>(g->atoms, g->na, g->cells, g->csign, g->crp, nc,
-                                              sys->mc_n);
+                                              g->mc_n);
     PB_LAUNCH_CHECK();
     return PB_OK;
 }

@@ -105,6 +105,8 @@ def test_crossing_list_bit_exact(pb, O, case):
     assert np.array_equal(pb.pb_get_array(g, "cross_alpha"), cr["alpha"])
     assert np.array_equal(pb.pb_get_array(g, "cross_rp"), cr["rp"])
     assert np.array_equal(pb.pb_get_array(g, "cross_sign"), cr["sign"])
+    assert np.array_equal(pb.pb_get_array(g, "mc_weight"), cr["mc_w"])
+    assert np.array_equal(pb.pb_get_array(g, "mc_normal"), cr["mc_n"])
 
 
 def _unknown_map(case):
@@ -178,7 +180,7 @@ def test_solve_residual_and_energy(pb, case, prec):
     assert np.max(np.abs(phi - refphi)) <= 1e-6 * np.max(np.abs(refphi))
     e = pb.pb_energy(s)
     er = ref["energy"]
-    for k in ("e_pol", "e_ion_flux", "e_ion_surf", "e_coul", "e_total"):
+    for k in ("e_pol", "e_ion_flux", "e_ion_surf", "e_coul", "e_total", "e_ion_mc"):
         assert abs(e[k] - er[k]) <= 1e-6 * max(abs(er[k]), 1e-3 * abs(er["e_pol"])), k
 
 

@@ -112,15 +112,18 @@ def test_single_level_tree_is_the_uniform_grid(O, orc):
     inter = op["kind"] == 0
     assert np.array_equal(op["mass"][inter], ref["coef"]["kap"][lin[inter]])
     assert np.max(np.abs(res["phi_pos"] - ref["phi"][lin])) <= 1e-12 * np.max(np.abs(ref["phi"]))
-    for k in ("e_pol", "e_ion_flux", "e_ion_surf", "e_total"):
+    for k in ("e_pol", "e_ion_flux", "e_ion_surf", "e_total", "e_ion_mc"):
         assert abs(res["energy"][k] - ref["energy"][k]) <= 1e-12 * abs(ref["energy"][k])
-    # the crossing list is the uniform one (same alpha, r_p, sign), in slot order
+    # the crossing list is the uniform one (same alpha, r_p, sign), in slot
+    # order, and so is its re-triangulated surface (weights, normals)
     cr = res["cross"]
     order = np.argsort(ref["cross"]["ids"])
     assert np.array_equal(np.sort(cr["ids"]), ref["cross"]["ids"][order])
     back = np.argsort(cr["ids"])
     for k in ("alpha", "rp", "sign"):
         assert np.array_equal(cr[k][back], ref["cross"][k][order])
+    assert np.array_equal(cr["mc_w"][back], ref["mc"]["W"][order])
+    assert np.array_equal(cr["mc_n"][back], ref["mc"]["normals"][order])
 
 
 @pytest.mark.parametrize("field", ["constant", "linear"])
@@ -196,7 +199,8 @@ def test_derefined_domain_with_null_bc(O, orc):
     100 %), Debye-Hueckel values do not (about 13 % at h = 0.5 A); on the
     de-refined domain (perfil 12.5 %, 1 A far-field cells) null values match
     the Debye-Hueckel result with a third of the unknowns of a uniform grid
-    over the same box.  E_pol is exact (Gauss) in every case."""
+    over the same box.  E_pol is exact (Gauss) in every case.  The
+    re-triangulated-surface E_ion beats the staircase one there."""
     lB, kD = orc.units(298.15, 0.145, 80.0)
     e_pol = 0.5 * (1 / 80.0 - 1 / 2.0) * lB / 2.0
     e_ion = -0.5 * lB / 80.0 * kD / (1.0 + kD * 2.0)
@@ -207,14 +211,18 @@ def test_derefined_domain_with_null_bc(O, orc):
         r = O.solve_problem(atoms, tree, bc=bc, rtol=1e-11)
         e = r["energy"]
         assert abs(e["e_pol"] - e_pol) < 1e-9 * abs(e_pol)
-        return tree, len(r["unk_slot"]), (e["e_ion_surf"] + e["e_ion_flux"] - e_ion) / abs(e_ion)
+        mc = (e["e_ion_mc"] + e["e_ion_flux"] - e_ion) / abs(e_ion)
+        return tree, len(r["unk_slot"]), (e["e_ion_surf"] + e["e_ion_flux"] - e_ion) / abs(e_ion), mc
 
-    _, _, tight_null = run(orc.BC_ZERO, h_fine=0.5, h_bulk=0.5, refine_dist=3.0, fill=1.25)
-    _, _, tight_dh = run(orc.BC_DH, h_fine=0.5, h_bulk=0.5, refine_dist=3.0, fill=1.25)
-    tree, unk, deref_null = run(orc.BC_ZERO, h_fine=0.5, h_bulk=4.0, refine_dist=3.0,
-                                fill=1 / 0.15, h_tight=0.5, tight_fill=1.25)
+    _, _, tight_null, _ = run(orc.BC_ZERO, h_fine=0.5, h_bulk=0.5, refine_dist=3.0, fill=1.25)
+    _, _, tight_dh, _ = run(orc.BC_DH, h_fine=0.5, h_bulk=0.5, refine_dist=3.0, fill=1.25)
+    tree, unk, deref_null, deref_mc = run(orc.BC_ZERO, h_fine=0.5, h_bulk=4.0, refine_dist=3.0,
+                                          fill=1 / 0.15, h_tight=0.5, tight_fill=1.25)
     assert abs(tight_null) > 1.0 and abs(tight_dh) < 0.2
     assert abs(deref_null) <= abs(tight_dh)
+    # the first integral on the re-triangulated surface (Sec. 3.3.2) halves
+    # the staircase error on the same de-refined domain
+    assert abs(deref_mc) < 0.6 * abs(deref_null)
     # a coarser far field around the tight box at h_tight (the 2:1 balance
     # grades the cells brick by brick, 8 cells per brick and level)
     assert tree.Lmax == 3 and set(np.unique(tree.blevel)) == {2, 3}
