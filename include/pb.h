@@ -137,7 +137,7 @@ typedef struct {
  * stencil, vectors and per-thread accumulation, FP64 global dots).
  * Stop when ||f - A phi||_2 <= rtol ||f||_2 (true residual, FP64).
  * max_iter caps the total inner iterations, max_outer the refinement
- * steps; inner_rtol (0 = default 1e-4) is the inner relative tolerance;
+ * steps; inner_rtol (0 = default 1e-6) is the inner relative tolerance;
  * time_budget_s (0 = none) bounds the wall time of the call. */
 typedef struct {
     int32_t precision;

@@ -130,7 +130,7 @@ struct HostSlot {
 
 struct Engine {
     int device = 0, cap = 0, chunk = 8;
-    double rtol = 1e-8, inner_rtol = 1e-4;
+    double rtol = 1e-8, inner_rtol = 1e-6;
     int max_iter = 100000, max_outer = 30;
     cudaStream_t cs = nullptr;
     EngineSlot *dslots = nullptr, *hmirror = nullptr;  // mirror: 2 x cap, pinned

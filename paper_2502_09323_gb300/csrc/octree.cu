@@ -2249,7 +2249,7 @@ pb_status oct_solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_s
     const int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     const double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
-    const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
+    const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-6;
     const BcDesc bd = bc_desc(sys);
     PB_CUDA_TRY(cudaMemcpyAsync(sys->phi, sys->bc, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     int iters = 0, outer = 0, status = PB_OK;

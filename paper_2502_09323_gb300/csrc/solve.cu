@@ -1329,7 +1329,7 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
     int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
-    double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
+    double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-6;
     int chunk = 16;
 
     // phi = boundary values, interior 0 (zero initial guess)

@@ -302,7 +302,7 @@ pb_status solve_split(pb_system *sys, int R, const pb_solve_opts *o, cudaStream_
     const int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     const double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
-    const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
+    const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-6;
 
     std::vector<Slab> sl(R);
     CgState **dsts = nullptr;
