@@ -7,9 +7,10 @@
 //
 // FP32 tiled kernel: sources staged in shared memory 256 at a time; each
 // position is stored as an FP32 pair (hi + lo) relative to the grid centre so
-// the difference r_t - r_i keeps ~46 bits; 1/r from rsqrtf; each tile's
-// contributions are summed with Kahan compensation in FP32 and the tile sum
-// is added to an FP64 accumulator.  A thread's two targets share each
+// the difference r_t - r_i keeps ~46 bits; 1/r from rsqrtf; a tile's
+// contributions are summed in groups of 16 in plain FP32, the group sums with
+// Kahan compensation in FP32, and the tile sum is added to an FP64
+// accumulator.  A thread's two targets share each
 // instruction through the packed FP32x2 arithmetic of sm_100-class GPUs.
 // It serves the surface terms Phi_p, Psi_p at the crossing points.
 //
@@ -26,6 +27,7 @@ namespace {
 
 constexpr int NB_THREADS = 256;
 constexpr int NB_TPT = 2;  // targets per thread
+constexpr int NB_GRP = 16; // sources per plainly summed group
 
 struct SrcHi {
     float x, y, z, q;
@@ -201,35 +203,45 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
         int m = (int)min((long long)NB_THREADS, ns - base);
         float2 sp = bc2(0.f), cp = bc2(0.f), sq = bc2(0.f), cq = bc2(0.f), s2 = bc2(0.f),
                c2 = bc2(0.f);
+        // groups of NB_GRP sources are summed plainly in FP32 (rounding error
+        // below (NB_GRP - 1) u of the group's absolute sum) and each group
+        // sum enters the tile sum with Kahan compensation
+        for (int q0 = 0; q0 < m; q0 += NB_GRP) {
+            const int q1 = min(q0 + NB_GRP, m);
+            float2 gp = bc2(0.f), gq = bc2(0.f), g2 = bc2(0.f);
 #pragma unroll 4
-        for (int q = 0; q < m; ++q) {
-            const float4 p0 = sp4[q][0], p1 = sp4[q][1], p2 = sp4[q][2], p3 = sp4[q][3];
-            const float2 dx = __fadd2_rn(sub2(th[0], make_float2(p0.x, p0.y)),
-                                         sub2(tl[0], make_float2(p2.x, p2.y)));
-            const float2 dy = __fadd2_rn(sub2(th[1], make_float2(p0.z, p0.w)),
-                                         sub2(tl[1], make_float2(p2.z, p2.w)));
-            const float2 dz = __fadd2_rn(sub2(th[2], make_float2(p1.x, p1.y)),
-                                         sub2(tl[2], make_float2(p3.x, p3.y)));
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f,
-                                          r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
-            float2 v = __fmul2_rn(make_float2(p1.z, p1.w), ri);
-            if (SCREEN) {
-                v.x *= expf(-kscr * (r2.x * ri.x));
-                v.y *= expf(-kscr * (r2.y * ri.y));
-            }
-            kahan_add2(sp, cp, v);
-            if (PSI) {
-                const float2 dn =
-                    __ffma2_rn(dz, tn[2], __ffma2_rn(dy, tn[1], __fmul2_rn(dx, tn[0])));
-                const float2 vr2 = __fmul2_rn(v, __fmul2_rn(ri, ri));
-                kahan_add2(sq, cq, __fmul2_rn(vr2, dn));
-                if (PSI2) {
-                    const float2 dn2 =
-                        __ffma2_rn(dz, tn2[2], __ffma2_rn(dy, tn2[1], __fmul2_rn(dx, tn2[0])));
-                    kahan_add2(s2, c2, __fmul2_rn(vr2, dn2));
+            for (int q = q0; q < q1; ++q) {
+                const float4 p0 = sp4[q][0], p1 = sp4[q][1], p2 = sp4[q][2], p3 = sp4[q][3];
+                const float2 dx = __fadd2_rn(sub2(th[0], make_float2(p0.x, p0.y)),
+                                             sub2(tl[0], make_float2(p2.x, p2.y)));
+                const float2 dy = __fadd2_rn(sub2(th[1], make_float2(p0.z, p0.w)),
+                                             sub2(tl[1], make_float2(p2.z, p2.w)));
+                const float2 dz = __fadd2_rn(sub2(th[2], make_float2(p1.x, p1.y)),
+                                             sub2(tl[2], make_float2(p3.x, p3.y)));
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f,
+                                              r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+                float2 v = __fmul2_rn(make_float2(p1.z, p1.w), ri);
+                if (SCREEN) {
+                    v.x *= expf(-kscr * (r2.x * ri.x));
+                    v.y *= expf(-kscr * (r2.y * ri.y));
+                }
+                gp = __fadd2_rn(gp, v);
+                if (PSI) {
+                    const float2 dn =
+                        __ffma2_rn(dz, tn[2], __ffma2_rn(dy, tn[1], __fmul2_rn(dx, tn[0])));
+                    const float2 vr2 = __fmul2_rn(v, __fmul2_rn(ri, ri));
+                    gq = __ffma2_rn(vr2, dn, gq);
+                    if (PSI2) {
+                        const float2 dn2 = __ffma2_rn(
+                            dz, tn2[2], __ffma2_rn(dy, tn2[1], __fmul2_rn(dx, tn2[0])));
+                        g2 = __ffma2_rn(vr2, dn2, g2);
+                    }
                 }
             }
+            kahan_add2(sp, cp, gp);
+            if (PSI) kahan_add2(sq, cq, gq);
+            if (PSI2) kahan_add2(s2, c2, g2);
         }
         acc_phi[0] += (double)sp.x - (double)cp.x;
         acc_phi[1] += (double)sp.y - (double)cp.y;
