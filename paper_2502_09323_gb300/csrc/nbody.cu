@@ -156,37 +156,15 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 v) {
     s = t;
 }
 
-// out_phi[t] = scale * sum_i q_i exp(-k r)/r; out_psi[t] = sum_i q_i (r.n)/r^3
-// (PSI only for surface targets); with PSI2 also out_psi2[t] along the
-// target's second normal, from the same pairs.  Self pairs (r == 0) are skipped.  Each
-// thread holds two targets in the two halves of FP32x2 registers; the
-// sources are staged in shared memory already duplicated into (v, v) pairs.
-static_assert(NB_TPT == 2, "two targets per thread, one per FP32x2 half");
-template <bool PSI, bool SCREEN, bool PSI2 = false>
-__global__ void __launch_bounds__(NB_THREADS)
-k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__ slo,
-        long long ns, float kscr, double scale, double *__restrict__ out_phi,
-        double *__restrict__ out_psi, double *__restrict__ out_psi2 = nullptr) {
-    // per source: (hx,hx,hy,hy) (hz,hz,q,q) (lx,lx,ly,ly) (lz,lz,0,0)
-    __shared__ float4 sp4[NB_THREADS][4];
-    long long t0 = ((long long)blockIdx.x * NB_THREADS * NB_TPT) + threadIdx.x;
-    TgtLoad tg[NB_TPT];
-    double acc_phi[NB_TPT], acc_psi[NB_TPT], acc_psi2[NB_TPT];
-#pragma unroll
-    for (int u = 0; u < NB_TPT; ++u) {
-        tg[u] = load_target(T, t0 + (long long)u * NB_THREADS);
-        acc_phi[u] = 0.0;
-        acc_psi[u] = 0.0;
-        acc_psi2[u] = 0.0;
-    }
-    float2 th[3], tl[3], tn[3], tn2[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        th[d] = make_float2(tg[0].h[d], tg[1].h[d]);
-        tl[d] = make_float2(tg[0].l[d], tg[1].l[d]);
-        tn[d] = make_float2(tg[0].n[d], tg[1].n[d]);
-        tn2[d] = make_float2(tg[0].n2[d], tg[1].n2[d]);
-    }
+// The source tiles of one block: per-pair work, group sums and tile sums as
+// described above, accumulated into acc_* (FP64).
+template <bool PSI, bool SCREEN, bool PSI2, int AXIS>
+__device__ __forceinline__ void nb_tiles(float4 (*sp4)[4], const float4 *__restrict__ shi,
+                                         const float4 *__restrict__ slo, long long ns, float kscr,
+                                         const float2 (&th)[3], const float2 (&tl)[3],
+                                         const float2 (&tn)[3], const float2 (&tn2)[3],
+                                         double (&acc_phi)[NB_TPT], double (&acc_psi)[NB_TPT],
+                                         double (&acc_psi2)[NB_TPT]) {
     for (long long base = 0; base < ns; base += NB_THREADS) {
         long long si = base + threadIdx.x;
         __syncthreads();
@@ -228,8 +206,17 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
                 }
                 gp = __fadd2_rn(gp, v);
                 if (PSI) {
+                    // Psi along n: the general dot product, or, for a
+                    // block whose targets all lie on edges along AXIS (n =
+                    // +-e_AXIS), that coordinate difference (sign applied to
+                    // the total)
                     const float2 dn =
-                        __ffma2_rn(dz, tn[2], __ffma2_rn(dy, tn[1], __fmul2_rn(dx, tn[0])));
+                        AXIS == 0 ? dx
+                                  : (AXIS == 1 ? dy
+                                               : (AXIS == 2 ? dz
+                                                            : __ffma2_rn(dz, tn[2],
+                                                                         __ffma2_rn(dy, tn[1],
+                                                                                    __fmul2_rn(dx, tn[0])))));
                     const float2 vr2 = __fmul2_rn(v, __fmul2_rn(ri, ri));
                     gq = __ffma2_rn(vr2, dn, gq);
                     if (PSI2) {
@@ -253,6 +240,76 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
             acc_psi2[0] += (double)s2.x - (double)c2.x;
             acc_psi2[1] += (double)s2.y - (double)c2.y;
         }
+    }
+}
+
+// out_phi[t] = scale * sum_i q_i exp(-k r)/r; out_psi[t] = sum_i q_i (r.n)/r^3
+// (PSI only for surface targets); with PSI2 also out_psi2[t] along the
+// target's second normal, from the same pairs.  Self pairs (r == 0) are skipped.  Each
+// thread holds two targets in the two halves of FP32x2 registers; the
+// sources are staged in shared memory already duplicated into (v, v) pairs.
+static_assert(NB_TPT == 2, "two targets per thread, one per FP32x2 half");
+template <bool PSI, bool SCREEN, bool PSI2 = false>
+__global__ void __launch_bounds__(NB_THREADS)
+k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__ slo,
+        long long ns, float kscr, double scale, double *__restrict__ out_phi,
+        double *__restrict__ out_psi, double *__restrict__ out_psi2 = nullptr) {
+    // per source: (hx,hx,hy,hy) (hz,hz,q,q) (lx,lx,ly,ly) (lz,lz,0,0)
+    __shared__ float4 sp4[NB_THREADS][4];
+    long long t0 = ((long long)blockIdx.x * NB_THREADS * NB_TPT) + threadIdx.x;
+    TgtLoad tg[NB_TPT];
+    double acc_phi[NB_TPT], acc_psi[NB_TPT], acc_psi2[NB_TPT];
+#pragma unroll
+    for (int u = 0; u < NB_TPT; ++u) {
+        tg[u] = load_target(T, t0 + (long long)u * NB_THREADS);
+        acc_phi[u] = 0.0;
+        acc_psi[u] = 0.0;
+        acc_psi2[u] = 0.0;
+    }
+    float2 th[3], tl[3], tn[3], tn2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        th[d] = make_float2(tg[0].h[d], tg[1].h[d]);
+        tl[d] = make_float2(tg[0].l[d], tg[1].l[d]);
+        tn[d] = make_float2(tg[0].n[d], tg[1].n[d]);
+        tn2[d] = make_float2(tg[0].n2[d], tg[1].n2[d]);
+    }
+    // a block whose targets all lie on edges of one direction (the
+    // crossing list is ordered by direction) takes the axis form of Psi
+    int axis = -1;
+    if (PSI && T.kind == TK_SURFACE) {
+        const long long tb = (long long)blockIdx.x * NB_THREADS * NB_TPT;
+        const int dref = (int)(T.ids[tb] / T.g.N);
+        bool same = true;
+#pragma unroll
+        for (int u = 0; u < NB_TPT; ++u) {
+            const long long t = t0 + (long long)u * NB_THREADS;
+            if (t < T.count && (int)(T.ids[t] / T.g.N) != dref) same = false;
+        }
+        if (__syncthreads_and(same)) axis = dref;
+    }
+    switch (axis) {
+        case 0:
+            nb_tiles<PSI, SCREEN, PSI2, 0>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
+                                           acc_psi, acc_psi2);
+            break;
+        case 1:
+            nb_tiles<PSI, SCREEN, PSI2, 1>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
+                                           acc_psi, acc_psi2);
+            break;
+        case 2:
+            nb_tiles<PSI, SCREEN, PSI2, 2>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
+                                           acc_psi, acc_psi2);
+            break;
+        default:
+            nb_tiles<PSI, SCREEN, PSI2, -1>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
+                                            acc_psi, acc_psi2);
+    }
+    if (PSI && axis >= 0) {
+        // n = sign e_axis: the one nonzero component is the sign
+#pragma unroll
+        for (int u = 0; u < NB_TPT; ++u)
+            acc_psi[u] *= (double)(tg[u].n[0] + tg[u].n[1] + tg[u].n[2]);
     }
 #pragma unroll
     for (int u = 0; u < NB_TPT; ++u) {
