@@ -20,7 +20,8 @@
 // fixed order without atomics.  k_mc_normal finds, through the atom cell
 // list, the ball whose sphere passes closest to the point (smallest
 // | |r_p - c| - R |, ties to the lower atom index) and takes the unit vector
-// from its centre.  This file is compiled without FMA contraction, so every
+// from its centre; an FP32 pass first bounds that minimum, so that the FP64
+// comparison only visits the candidates that can reach it.  This file is compiled without FMA contraction, so every
 // value is reproducible to the bit.
 #include <math.h>
 
@@ -174,10 +175,26 @@ k_mc_weight(GridGeo g, const uint8_t *__restrict__ inside, const long long *__re
     W[s] = w;
 }
 
+// FP32 copies of the atoms relative to the cell list's corner: (x, y, z, R)
+__global__ void k_atoms32(const double *__restrict__ atoms, long long na, CellList cl,
+                          float4 *__restrict__ a32) {
+    const long long i = blockIdx.x * 128ll + threadIdx.x;
+    if (i >= na) return;
+    a32[i] = make_float4((float)(atoms[i] - cl.lo[0]), (float)(atoms[na + i] - cl.lo[1]),
+                         (float)(atoms[2 * na + i] - cl.lo[2]), (float)atoms[3 * na + i]);
+}
+
+// |r - c| - R in FP32 differs from the FP64 value by at most about
+// 4 * 2^-24 * X, X the largest coordinate relative to the cell list's corner
+// (each rounding of a coordinate to FP32 costs 2^-24 X, the difference and
+// the distance add rounding of their own); a candidate whose FP32 value
+// exceeds the FP32 minimum by more than twice that bound can be neither the
+// FP64 minimum nor tied with it.  The margin passed in is several times that.
+
 __global__ void __launch_bounds__(128)
-k_mc_normal(const double *__restrict__ atoms, long long na, CellList cl,
-            const int8_t *__restrict__ sign, const double *__restrict__ rp, long long ncross,
-            double *__restrict__ nrm) {
+k_mc_normal(const double *__restrict__ atoms, const float4 *__restrict__ a32, long long na,
+            CellList cl, float margin, const int8_t *__restrict__ sign,
+            const double *__restrict__ rp, long long ncross, double *__restrict__ nrm) {
     const long long s = blockIdx.x * 128ll + threadIdx.x;
     if (s >= ncross) return;
     double o0 = 0.0, o1 = 0.0, o2 = 0.0;
@@ -189,6 +206,28 @@ k_mc_normal(const double *__restrict__ atoms, long long na, CellList cl,
             const double u = floor((p[q] - cl.lo[q]) / cl.cs);
             cc[q] = (u < -4.0) ? -4 : ((u > (double)cl.dim[q] + 4.0) ? cl.dim[q] + 4 : (int)u);
         }
+        const float f0 = (float)(p0 - cl.lo[0]), f1 = (float)(p1 - cl.lo[1]),
+                    f2 = (float)(p2 - cl.lo[2]);
+        // pass 1: the smallest FP32 deviation
+        float m32 = INFINITY;
+        for (int cz = cc[2] - 1; cz <= cc[2] + 1; ++cz) {
+            if (cz < 0 || cz >= cl.dim[2]) continue;
+            for (int cy = cc[1] - 1; cy <= cc[1] + 1; ++cy) {
+                if (cy < 0 || cy >= cl.dim[1]) continue;
+                for (int cx = cc[0] - 1; cx <= cc[0] + 1; ++cx) {
+                    if (cx < 0 || cx >= cl.dim[0]) continue;
+                    const int cid = (cz * cl.dim[1] + cy) * cl.dim[0] + cx;
+                    for (int q = cl.start[cid]; q < cl.start[cid + 1]; ++q) {
+                        const float4 a = a32[cl.atom[q]];
+                        const float dx = f0 - a.x, dy = f1 - a.y, dz = f2 - a.z;
+                        m32 = fminf(m32, fabsf(sqrtf(dx * dx + dy * dy + dz * dz) - a.w));
+                    }
+                }
+            }
+        }
+        // pass 2: the FP64 comparison, in the same order, over the
+        // candidates that can win
+        const float lim = m32 + margin;
         long long best = -1;
         double bdev = 0.0, bd = 0.0;
         for (int cz = cc[2] - 1; cz <= cc[2] + 1; ++cz) {
@@ -200,6 +239,9 @@ k_mc_normal(const double *__restrict__ atoms, long long na, CellList cl,
                     const int cid = (cz * cl.dim[1] + cy) * cl.dim[0] + cx;
                     for (int q = cl.start[cid]; q < cl.start[cid + 1]; ++q) {
                         const long long at = cl.atom[q];
+                        const float4 a = a32[at];
+                        const float ex = f0 - a.x, ey = f1 - a.y, ez = f2 - a.z;
+                        if (fabsf(sqrtf(ex * ex + ey * ey + ez * ez) - a.w) > lim) continue;
                         const double dx = p0 - atoms[at], dy = p1 - atoms[na + at],
                                      dz = p2 - atoms[2 * na + at];
                         const double dd = sqrt((dx * dx + dy * dy) + dz * dz);
@@ -237,9 +279,22 @@ pb_status mc_surface(pb_grid *g, cudaStream_t s) {
     k_mc_weight<<<cdiv(nc, 128), 128, 0, s>>>(g->geo, g->inside, g->cid, g->rowstart, g->csign,
                                               g->crp, nc, g->mc_w);
     PB_LAUNCH_CHECK();
-    k_mc_normal<<<cdiv(nc, 128), 128, 0, s>>>(g->atoms, g->na, g->cells, g->csign, g->crp, nc,
-                                              g->mc_n);
+    float4 *a32 = (float4 *)dalloc(sizeof(float4) * (size_t)(g->na > 0 ? g->na : 1), s);
+    if (!a32) return PB_ERR_OOM;
+    if (g->na > 0) {
+        k_atoms32<<<cdiv(g->na, 128), 128, 0, s>>>(g->atoms, g->na, g->cells, a32);
+        PB_LAUNCH_CHECK();
+    }
+    // coordinates of the searched points and atoms stay within the cell
+    // list's box widened by four cells on each side
+    const CellList &cl = g->cells;
+    double ext = 0.0;
+    for (int q = 0; q < 3; ++q) ext = fmax(ext, (double)(cl.dim[q] + 8) * cl.cs);
+    const float margin = (float)(1e-3 + 64.0 * ext * 5.9604644775390625e-8);
+    k_mc_normal<<<cdiv(nc, 128), 128, 0, s>>>(g->atoms, a32, g->na, cl, margin, g->csign, g->crp,
+                                              nc, g->mc_n);
     PB_LAUNCH_CHECK();
+    dfree(a32, s);
     return PB_OK;
 }
 
