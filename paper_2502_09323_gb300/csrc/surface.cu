@@ -58,68 +58,89 @@ __device__ long long find_edge(const long long *__restrict__ ids, const int *__r
     return -1;
 }
 
-// Triangles of cell (i, j, k): crossing-list indices (fan order) and areas.
-__device__ int mc_cell(const GridGeo &g, const uint8_t *__restrict__ inside,
-                       const long long *__restrict__ ids, const int *__restrict__ rowstart,
-                       const double *__restrict__ rp, long long i, long long j, long long k,
-                       long long (*tri)[3], double *area) {
-    long long node[8];
+// Adds to w, in fan order, T/3 of every triangle of cell (ci, cj, ck) that
+// has the cell edge es (the crossing point s) as a vertex.  The cell's
+// state lives in registers: the neighbours of each crossed cell edge as
+// 4-bit fields (filled in face order, first neighbour first), a loop as a
+// string of 4-bit edge indices.
+__device__ void mc_cell_acc(const GridGeo &g, const uint8_t *__restrict__ inside,
+                            const long long *__restrict__ ids, const int *__restrict__ rowstart,
+                            const double *__restrict__ rp, long long ci, long long cj,
+                            long long ck, int es, double &w) {
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const long long n0 = (ck * g.ny + cj) * g.nx + ci;
+    auto node = [&](int c) -> long long {
+        return n0 + (c & 1) + ((c >> 1) & 1) * sy + ((c >> 2) & 1) * sz;
+    };
     int ins = 0;
-    for (int c = 0; c < 8; ++c) {
-        node[c] = ((k + ((c >> 2) & 1)) * g.ny + (j + ((c >> 1) & 1))) * g.nx + (i + (c & 1));
-        if (inside[node[c]]) ins |= 1 << c;
-    }
-    if (ins == 0 || ins == 0xff) return 0;
-    long long vert[12];
-    for (int e = 0; e < 12; ++e) {
-        const int ca = c_edge_corner[e][0], cb = c_edge_corner[e][1];
-        vert[e] = -1;
-        if (((ins >> ca) ^ (ins >> cb)) & 1)
-            vert[e] = find_edge(ids, rowstart, g.nx, (long long)(e / 4) * g.N + node[ca]);
-    }
-    int nbr[12][2], deg[12];
-    for (int e = 0; e < 12; ++e) deg[e] = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (inside[node(c)]) ins |= 1 << c;
+    if (ins == 0 || ins == 0xff) return;
+    unsigned cm = 0;  // crossed cell edges
+#pragma unroll
+    for (int e = 0; e < 12; ++e)
+        if (((ins >> c_edge_corner[e][0]) ^ (ins >> c_edge_corner[e][1])) & 1) cm |= 1u << e;
+    if (!((cm >> es) & 1)) return;
+    unsigned long long nb0 = 0, nb1 = 0;
+    unsigned has0 = 0;
+    auto link = [&](int a, int b) {
+        if (!((has0 >> a) & 1)) {
+            nb0 |= (unsigned long long)b << (4 * a);
+            has0 |= 1u << a;
+        } else {
+            nb1 |= (unsigned long long)b << (4 * a);
+        }
+    };
+#pragma unroll
     for (int f = 0; f < 6; ++f) {
-        int cr[4], m = 0;
+        int crp = 0, m = 0;
+#pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (((ins >> c_face[f][q]) ^ (ins >> c_face[f][(q + 1) & 3])) & 1) cr[m++] = q;
-        int pa[2], pb[2], np = 0;
+            if (((ins >> c_face[f][q]) ^ (ins >> c_face[f][(q + 1) & 3])) & 1) {
+                crp |= q << (2 * m);
+                ++m;
+            }
         if (m == 2) {
-            pa[0] = c_face_edge[f][cr[0]];
-            pb[0] = c_face_edge[f][cr[1]];
-            np = 1;
+            const int a = c_face_edge[f][crp & 3], b = c_face_edge[f][(crp >> 2) & 3];
+            link(a, b);
+            link(b, a);
         } else if (m == 4) {
             // cut off each inside corner (corner q lies between face edges q-1 and q)
             const int q0 = ((ins >> c_face[f][0]) & 1) ? 0 : 1;
-            pa[0] = c_face_edge[f][(q0 + 3) & 3];
-            pb[0] = c_face_edge[f][q0];
-            pa[1] = c_face_edge[f][(q0 + 1) & 3];
-            pb[1] = c_face_edge[f][(q0 + 2) & 3];
-            np = 2;
-        }
-        for (int p = 0; p < np; ++p) {
-            nbr[pa[p]][deg[pa[p]]++] = pb[p];
-            nbr[pb[p]][deg[pb[p]]++] = pa[p];
+            const int pa0 = c_face_edge[f][(q0 + 3) & 3], pb0 = c_face_edge[f][q0];
+            const int pa1 = c_face_edge[f][(q0 + 1) & 3], pb1 = c_face_edge[f][(q0 + 2) & 3];
+            link(pa0, pb0);
+            link(pb0, pa0);
+            link(pa1, pb1);
+            link(pb1, pa1);
         }
     }
-    int seen = 0, nt = 0;
+    auto vert = [&](int e) -> long long {
+        return find_edge(ids, rowstart, g.nx, (long long)(e / 4) * g.N + node(c_edge_corner[e][0]));
+    };
+    unsigned seen = 0;
     for (int e0 = 0; e0 < 12; ++e0) {
-        const int ca = c_edge_corner[e0][0], cb = c_edge_corner[e0][1];
-        if (!(((ins >> ca) ^ (ins >> cb)) & 1) || ((seen >> e0) & 1)) continue;
-        int loop[12], len = 0;
-        int prev = e0;
-        int cur = nbr[e0][0] < nbr[e0][1] ? nbr[e0][0] : nbr[e0][1];
-        loop[len++] = e0;
-        seen |= 1 << e0;
+        if (!((cm >> e0) & 1) || ((seen >> e0) & 1)) continue;
+        unsigned long long lp = (unsigned long long)e0;
+        int len = 1, prev = e0;
+        const int f0 = (int)((nb0 >> (4 * e0)) & 15), f1 = (int)((nb1 >> (4 * e0)) & 15);
+        int cur = f0 < f1 ? f0 : f1;
+        seen |= 1u << e0;
         while (cur != e0 && len < 12) {
-            loop[len++] = cur;
-            seen |= 1 << cur;
-            const int nx = nbr[cur][0] == prev ? nbr[cur][1] : nbr[cur][0];
+            lp |= (unsigned long long)cur << (4 * len);
+            ++len;
+            seen |= 1u << cur;
+            const int a0 = (int)((nb0 >> (4 * cur)) & 15), a1 = (int)((nb1 >> (4 * cur)) & 15);
+            const int nx = a0 == prev ? a1 : a0;
             prev = cur;
             cur = nx;
         }
         for (int m = 1; m + 1 < len; ++m) {
-            const long long a = vert[loop[0]], b = vert[loop[m]], c = vert[loop[m + 1]];
+            const int ea = (int)(lp & 15), eb = (int)((lp >> (4 * m)) & 15),
+                      ec = (int)((lp >> (4 * (m + 1))) & 15);
+            if (ea != es && eb != es && ec != es) continue;
+            const long long a = vert(ea), b = vert(eb), c = vert(ec);
             if (a < 0 || b < 0 || c < 0) continue;
             const double *p0 = rp + 3 * a, *p1 = rp + 3 * b, *p2 = rp + 3 * c;
             const double u0 = p1[0] - p0[0], u1 = p1[1] - p0[1], u2 = p1[2] - p0[2];
@@ -127,14 +148,9 @@ __device__ int mc_cell(const GridGeo &g, const uint8_t *__restrict__ inside,
             const double x = u1 * v2 - u2 * v1;
             const double y = u2 * v0 - u0 * v2;
             const double z = u0 * v1 - u1 * v0;
-            tri[nt][0] = a;
-            tri[nt][1] = b;
-            tri[nt][2] = c;
-            area[nt] = 0.5 * sqrt((x * x + y * y) + z * z);
-            ++nt;
+            w += 0.5 * sqrt((x * x + y * y) + z * z) / 3.0;
         }
     }
-    return nt;
 }
 
 __global__ void __launch_bounds__(128)
@@ -149,9 +165,9 @@ k_mc_weight(GridGeo g, const uint8_t *__restrict__ inside, const long long *__re
         const int d = (int)(id / g.N);
         const long long a = id - (long long)d * g.N;
         const long long i = a % g.nx, j = (a / g.nx) % g.ny, k = a / ((long long)g.nx * g.ny);
-        long long tri[12][3];
-        double area[12];
-        // the (up to) four cells around the edge, in node order
+        // the (up to) four cells around the edge, in node order; the edge's
+        // index in each: x edges 0-3 by (dy + 2 dz), y edges 4-7 by
+        // (dx + 2 dz), z edges 8-11 by (dx + 2 dy), offsets from the cell
         for (int v = 0; v < 2; ++v)
             for (int u = 0; u < 2; ++u) {
                 long long ci = i, cj = j, ck = k;
@@ -167,9 +183,9 @@ k_mc_weight(GridGeo g, const uint8_t *__restrict__ inside, const long long *__re
                 }
                 if (ci < 0 || cj < 0 || ck < 0 || ci > g.nx - 2 || cj > g.ny - 2 || ck > g.nz - 2)
                     continue;
-                const int nt = mc_cell(g, inside, ids, rowstart, rp, ci, cj, ck, tri, area);
-                for (int t = 0; t < nt; ++t)
-                    if (tri[t][0] == s || tri[t][1] == s || tri[t][2] == s) w += area[t] / 3.0;
+                const int ox = (int)(i - ci), oy = (int)(j - cj), oz = (int)(k - ck);
+                const int es = d == 0 ? oy + 2 * oz : (d == 1 ? 4 + ox + 2 * oz : 8 + ox + 2 * oy);
+                mc_cell_acc(g, inside, ids, rowstart, rp, ci, cj, ck, es, w);
             }
     }
     W[s] = w;
