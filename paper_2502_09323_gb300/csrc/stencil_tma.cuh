@@ -20,8 +20,10 @@
 // (planes k and k+1) and keeps its own row of planes k-1, k in registers, so
 // the producer runs up to NSLOT-2 planes ahead of the slowest warp.  No
 // consumer ever waits on another consumer.  Rows without listed edges take
-// a packed FP32x2 fast path; rows with listed edges gather their weights
-// (the update kernel prefetches the next plane's into L1).
+// a packed FP32x2 fast path; rows with listed edges gather their weights,
+// issued as soon as the plane's codes are at hand and before the warp waits
+// for the next plane, so the gathers overlap that wait (the update kernel
+// also prefetches the next plane's into L1).
 //
 // Dot products: each item's go to that item's own FP32 slot; the last block
 // of the launch sums every system's slots in an order fixed by its item
@@ -507,36 +509,12 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             }
             for (int t = 1; ok && t <= len; ++t) {
                 const int k = kfirst + t - 1;
-                if (!wait_full(gt0 + t + 1)) {
-                    ok = false;
-                    break;
-                }
                 const uint8_t *sc = slot_ptr(gt0 + t), *sn = slot_ptr(gt0 + t + 1);
-                val4(sn, r, pn);
-                cn = code4(sn, r);
-                if (MODE == MODE_U && t < len) prefetch_w(sn, k + 1, j, ib, cn, 0u);
-                float ym[4], yp[4];
-                val4(sc, r - 1, ym);
-                val4(sc, r + 1, yp);
+                // plane t's codes are all here (its slot is full): decide the
+                // path and issue the listed-weight gathers first, so that they
+                // are in flight while this warp waits for plane t+1
                 const uint32_t cym = code4(sc, r - 1);
-                float left = __shfl_up_sync(0xffffffffu, pc[3], 1);
-                float right = __shfl_down_sync(0xffffffffu, pc[0], 1);
-                if (lane == 0) left = val1(sc, r, 3);
-                if (lane == 31) right = val1(sc, r, 4 + 32 * 4);
                 const uint32_t lcode = sc[L::code + r * CODEW + 15 + lane * 4];
-                float xv[4] = {0.f, 0.f, 0.f, 0.f}, zv[4] = {0.f, 0.f, 0.f, 0.f};
-                if (MODE == MODE_U) {
-                    float4 a = *reinterpret_cast<const float4 *>(sc + L::x + (w * OWNW + lane * 4) * 4);
-                    float4 b = *reinterpret_cast<const float4 *>(sc + L::z + (w * OWNW + lane * 4) * 4);
-                    xv[0] = a.x;
-                    xv[1] = a.y;
-                    xv[2] = a.z;
-                    xv[3] = a.w;
-                    zv[0] = b.x;
-                    zv[1] = b.y;
-                    zv[2] = b.z;
-                    zv[3] = b.w;
-                }
                 const uint32_t cxl = (cc << 8) | lcode;
                 const uint32_t special = (cc & 0x0E0E0E0Eu) | (cxl & 0x02020202u) |
                                          (cym & 0x04040404u) | (cm & 0x08080808u);
@@ -544,6 +522,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 const int base = k * (int)g.sxy + j * g.sx;
                 // per-point weights of the six faces
                 float wxp[4], wxm[4], wyp[4], wym[4], wzp[4], wzm[4];
+                float wl = 0.f;
                 if (fast) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -551,7 +530,6 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                         wxp[q] = wxm[q] = wyp[q] = wym[q] = wzp[q] = wzm[q] = wp;
                     }
                 } else {
-                    // issue every listed-weight load first, then use them
                     const bool wz_valid = t > 1;
                     const int pl = base + ib;
 #pragma unroll
@@ -567,13 +545,39 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                         wzm[q] = wz_valid ? wzc[q]
                                           : ((cz & 8) ? __ldg(cp.wz + pl + q - (int)g.sxy) : wp);
                     }
+                    if (lane == 0) wl = (lcode & 2) ? __ldg(cp.wx + pl - 1) : cp.pure((uint8_t)cc);
+                }
+                if (!wait_full(gt0 + t + 1)) {
+                    ok = false;
+                    break;
+                }
+                val4(sn, r, pn);
+                cn = code4(sn, r);
+                if (MODE == MODE_U && t < len) prefetch_w(sn, k + 1, j, ib, cn, 0u);
+                float ym[4], yp[4];
+                val4(sc, r - 1, ym);
+                val4(sc, r + 1, yp);
+                float left = __shfl_up_sync(0xffffffffu, pc[3], 1);
+                float right = __shfl_down_sync(0xffffffffu, pc[0], 1);
+                if (lane == 0) left = val1(sc, r, 3);
+                if (lane == 31) right = val1(sc, r, 4 + 32 * 4);
+                float xv[4] = {0.f, 0.f, 0.f, 0.f}, zv[4] = {0.f, 0.f, 0.f, 0.f};
+                if (MODE == MODE_U) {
+                    float4 a = *reinterpret_cast<const float4 *>(sc + L::x + (w * OWNW + lane * 4) * 4);
+                    float4 b = *reinterpret_cast<const float4 *>(sc + L::z + (w * OWNW + lane * 4) * 4);
+                    xv[0] = a.x;
+                    xv[1] = a.y;
+                    xv[2] = a.z;
+                    xv[3] = a.w;
+                    zv[0] = b.x;
+                    zv[1] = b.y;
+                    zv[2] = b.z;
+                    zv[3] = b.w;
+                }
+                if (!fast) {
                     // -x weight of point q is the +x weight of point q-1
-                    float wl = __shfl_up_sync(0xffffffffu, wxp[3], 1);
-                    if (lane == 0) {
-                        const uint8_t c0 = (uint8_t)cc;
-                        wl = (lcode & 2) ? __ldg(cp.wx + pl - 1) : cp.pure(c0);
-                    }
-                    wxm[0] = wl;
+                    const float wsh = __shfl_up_sync(0xffffffffu, wxp[3], 1);
+                    wxm[0] = lane == 0 ? wl : wsh;
                     wxm[1] = wxp[0];
                     wxm[2] = wxp[1];
                     wxm[3] = wxp[2];
