@@ -16,9 +16,11 @@
 //   * the code bytes on a 160 x 10 box,
 // into a ring of NSLOT shared-memory slots, each guarded by a "full" mbarrier
 // (transaction bytes) and an "empty" mbarrier (one arrival per consumer warp).
-// The 8 consumer warps compute one row each; a warp holds at most two slots
-// (planes k and k+1) and keeps its own row of planes k-1, k in registers, so
-// the producer runs up to NSLOT-2 planes ahead of the slowest warp.  No
+// The 8 consumer warps compute one row each; a warp reads everything it
+// needs from plane k's slot (its row, the rows above and below, the x-edge
+// neighbours, codes) and releases it before it waits for plane k+1, keeping
+// its own row of planes k-1, k, k+1 in registers, so the producer runs up to
+// NSLOT-1 planes ahead of the slowest warp.  No
 // consumer ever waits on another consumer.  Rows without listed edges take
 // a packed FP32x2 fast path; rows with listed edges gather their weights,
 // issued as soon as the plane's codes are at hand and before the warp waits
@@ -547,13 +549,6 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                     }
                     if (lane == 0) wl = (lcode & 2) ? __ldg(cp.wx + pl - 1) : cp.pure((uint8_t)cc);
                 }
-                if (!wait_full(gt0 + t + 1)) {
-                    ok = false;
-                    break;
-                }
-                val4(sn, r, pn);
-                cn = code4(sn, r);
-                if (MODE == MODE_U && t < len) prefetch_w(sn, k + 1, j, ib, cn, 0u);
                 float ym[4], yp[4];
                 val4(sc, r - 1, ym);
                 val4(sc, r + 1, yp);
@@ -574,6 +569,16 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                     zv[2] = b.z;
                     zv[3] = b.w;
                 }
+                // every read of plane t's slot is done: release it before waiting
+                // for plane t+1, so a warp holds one slot at a time
+                release(gt0 + t);
+                if (!wait_full(gt0 + t + 1)) {
+                    ok = false;
+                    break;
+                }
+                val4(sn, r, pn);
+                cn = code4(sn, r);
+                if (MODE == MODE_U && t < len) prefetch_w(sn, k + 1, j, ib, cn, 0u);
                 if (!fast) {
                     // -x weight of point q is the +x weight of point q-1
                     const float wsh = __shfl_up_sync(0xffffffffu, wxp[3], 1);
@@ -686,7 +691,6 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) wzc[q] = wzp[q];
-                release(gt0 + t);
                 if (grp_ok) {
                     if (MODE == MODE_P)
                         *reinterpret_cast<float4 *>(outp + base + ib) = make_float4(pc[0], pc[1], pc[2], pc[3]);
