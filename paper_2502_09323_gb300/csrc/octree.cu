@@ -1157,6 +1157,20 @@ __device__ __forceinline__ void kahan(float &s, float &c, float v) {
     s = t;
 }
 
+// 4-byte asynchronous copy global -> shared (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // named barrier of one 64-thread brick group (ids 1-4; 0 is __syncthreads)
 __device__ __forceinline__ void group_sync(int g) {
     switch (g) {
@@ -1173,6 +1187,15 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
     __shared__ T sv[4][8 * PP];
     __shared__ uint8_t sc[4][8 * PP];
     __shared__ int snb[4][6];
+    // FP32 update kernel: the listed +x, +y, +z weights of each group's
+    // brick (512 each), copied in asynchronously with the brick's values.
+    // (The direction kernel keeps gathering them: the 15 KB more shared
+    // memory per block, at its four blocks per SM, cost it more L1 than
+    // the copies saved: 270 -> 290 us on the 20,000-atom octree, against
+    // 331 -> 311 us for the update kernel.)
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr bool AW = F32 && MODE == OM_U;
+    __shared__ float swt[AW ? 4 * 3 * 512 : 1];
     const OctDev &t = A.t;
     const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
     const int i = c & 7, j = c >> 3;
@@ -1197,6 +1220,19 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
     // shared-memory store and the brick waits on one memory latency, not two.
     const int bstride = gridDim.x * 4;
     int pf_f = -1, pf_zm = -1, pf_zp = -1, pf_s = -1;
+    // (FP32) this column's code bytes are read one brick ahead too, so that
+    // the brick's listed weights are copied in the same round trip as its
+    // values instead of being gathered after the codes arrive
+    unsigned long long pf_cd = 0ull;
+    auto load_codes = [&](int bb) -> unsigned long long {
+        unsigned long long w8 = 0ull;
+        const int bs = (bb << 9) + c;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w8 |= (unsigned long long)A.code[bs + 64 * k] << (8 * k);
+        return w8;
+    };
+    float *W1 = AW ? swt + g * 1536 : nullptr, *W3 = AW ? W1 + 512 : nullptr,
+          *W5 = AW ? W1 + 1024 : nullptr;
     {
         const int b0 = blockIdx.x * 4 + g;
         if (b0 < nb) {
@@ -1204,18 +1240,21 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
             pf_zm = t.bnbr[6 * b0 + 4];
             pf_zp = t.bnbr[6 * b0 + 5];
             if (c < 6) pf_s = t.bnbr[6 * b0 + c];
+            if constexpr (AW) pf_cd = load_codes(b0);
         }
     }
     for (int b = blockIdx.x * 4 + g; b < nb; b += bstride) {
         const int nbk = pf_f, nzm = pf_zm, nzp = pf_zp;
         group_sync(g);  // the group's previous brick is done with its buffers
         if (c < 6) snb[g][c] = pf_s;
+        const unsigned long long cdw = pf_cd;
         if (b + bstride < nb) {
             const int bn = b + bstride;
             pf_f = t.bnbr[6 * bn + f];
             pf_zm = t.bnbr[6 * bn + 4];
             pf_zp = t.bnbr[6 * bn + 5];
             if (c < 6) pf_s = t.bnbr[6 * bn + c];
+            if constexpr (AW) pf_cd = load_codes(bn);
         }
         const int level = t.blow[b].w;
         T wi = 0, wo = 0, kp = 0;
@@ -1227,9 +1266,20 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
         const int base = (b << 9) + c;
         T v[8], xr[MODE == OM_U ? 8 : 1], zr[MODE == OM_U ? 8 : 1];
         uint8_t cd[8];
+        if constexpr (AW) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cd[k] = (uint8_t)(cdw >> (8 * k));
+                const int a = base + 64 * k;
+                if (cd[k] & 2) cp_async4(W1 + 64 * k + c, A.w32[0] + a);
+                if (cd[k] & 4) cp_async4(W3 + 64 * k + c, A.w32[1] + a);
+                if (cd[k] & 8) cp_async4(W5 + 64 * k + c, A.w32[2] + a);
+            }
+            cp_async_commit();
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            cd[k] = A.code[base + 64 * k];
+            if constexpr (!AW) cd[k] = A.code[base + 64 * k];
             v[k] = value(base + 64 * k, cd[k]);
             if constexpr (MODE == OM_U) {
                 xr[k] = A.x[base + 64 * k];
@@ -1274,7 +1324,8 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
             V[sq] = hv[r];
             C[sq] = hc[r];
         }
-        group_sync(g);  // staged planes and snb visible
+        if constexpr (AW) cp_async_wait_all();
+        group_sync(g);  // staged planes, weights and snb visible
         float bs0 = 0.f, bs1 = 0.f;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -1293,15 +1344,38 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
                 const uint8_t cxm = C[q - 1], cym = C[q - PX];
                 const uint8_t czmk = k > 0 ? cd[k - 1] : czm;
                 const T wself = (cc & 1) ? wi : wo;
-                w[1] = (cc & 2) ? A.w32[0][a] : wself;
-                w[3] = (cc & 4) ? A.w32[1][a] : wself;
-                w[5] = (cc & 8) ? A.w32[2][a] : wself;
-                if (cxm & 2) w[0] = A.w32[0][i > 0 ? a - 1 : (snb[g][0] << 9) + (a & 511) + 7];
-                else w[0] = (cxm & 1) ? wi : wo;
-                if (cym & 4) w[2] = A.w32[1][j > 0 ? a - 8 : (snb[g][2] << 9) + (a & 511) + 56];
-                else w[2] = (cym & 1) ? wi : wo;
-                if (czmk & 8) w[4] = A.w32[2][k > 0 ? a - 64 : (nzm << 9) + (a & 511) + 448];
-                else w[4] = (czmk & 1) ? wi : wo;
+                if constexpr (AW) {
+                    // listed weights of the brick's own edges from shared
+                    // memory, of edges into a neighbouring brick gathered
+                    w[1] = (cc & 2) ? W1[64 * k + c] : wself;
+                    w[3] = (cc & 4) ? W3[64 * k + c] : wself;
+                    w[5] = (cc & 8) ? W5[64 * k + c] : wself;
+                    if (cxm & 2)
+                        w[0] = i > 0 ? W1[64 * k + c - 1]
+                                     : A.w32[0][(snb[g][0] << 9) + (a & 511) + 7];
+                    else
+                        w[0] = (cxm & 1) ? wi : wo;
+                    if (cym & 4)
+                        w[2] = j > 0 ? W3[64 * k + c - 8]
+                                     : A.w32[1][(snb[g][2] << 9) + (a & 511) + 56];
+                    else
+                        w[2] = (cym & 1) ? wi : wo;
+                    if (czmk & 8)
+                        w[4] = k > 0 ? W5[64 * (k - 1) + c]
+                                     : A.w32[2][(nzm << 9) + (a & 511) + 448];
+                    else
+                        w[4] = (czmk & 1) ? wi : wo;
+                } else {
+                    w[1] = (cc & 2) ? A.w32[0][a] : wself;
+                    w[3] = (cc & 4) ? A.w32[1][a] : wself;
+                    w[5] = (cc & 8) ? A.w32[2][a] : wself;
+                    if (cxm & 2) w[0] = A.w32[0][i > 0 ? a - 1 : (snb[g][0] << 9) + (a & 511) + 7];
+                    else w[0] = (cxm & 1) ? wi : wo;
+                    if (cym & 4) w[2] = A.w32[1][j > 0 ? a - 8 : (snb[g][2] << 9) + (a & 511) + 56];
+                    else w[2] = (cym & 1) ? wi : wo;
+                    if (czmk & 8) w[4] = A.w32[2][k > 0 ? a - 64 : (nzm << 9) + (a & 511) + 448];
+                    else w[4] = (czmk & 1) ? wi : wo;
+                }
             } else {
                 w[0] = A.W[0][i > 0 ? a - 1 : (snb[g][0] << 9) + (a & 511) + 7];
                 w[1] = A.W[0][a];
