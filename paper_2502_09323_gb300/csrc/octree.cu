@@ -1421,15 +1421,41 @@ __global__ void __launch_bounds__(OB, MODE == OM_U ? 3 : 4) k_oct_pure(OctArgs<T
         }
     }
     // level-transition rows (explicit CSR): each block takes a fixed
-    // contiguous range of rows, one row per thread at a time
+    // contiguous range of rows, one row per thread at a time (rows r0 + tid,
+    // + OB, + 2 OB, ...).  The bounds of the row after next are read, and
+    // the next row's entries brought into L1, while a row is summed, so a
+    // row waits on its value gathers only.
     if (A.ntr > 0) {
         const long long per = (A.ntr + gridDim.x - 1) / gridDim.x;
         const long long r0 = (long long)blockIdx.x * per;
         const long long r1 = min(A.ntr, r0 + per);
+        long long na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;  // bounds of rows r + OB, r + 2 OB
+        {
+            const long long r = r0 + threadIdx.x;
+            if (r < r1) {
+                na0 = A.tr_ptr[r];
+                na1 = A.tr_ptr[r + 1];
+            }
+            if (r + OB < r1) {
+                nb0 = A.tr_ptr[r + OB];
+                nb1 = A.tr_ptr[r + OB + 1];
+            }
+        }
         for (long long r = r0 + threadIdx.x; r < r1; r += OB) {
+            const long long e0 = na0, e1 = na1;
+            na0 = nb0;
+            na1 = nb1;
+            if (r + 2 * OB < r1) {
+                nb0 = A.tr_ptr[r + 2 * OB];
+                nb1 = A.tr_ptr[r + 2 * OB + 1];
+            }
+            if (r + OB < r1 && na1 > na0) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.tr_col + na0));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.tr_val + na0));
+            }
             const int a = A.tr_slot[r];
             T q = 0;
-            for (long long e = A.tr_ptr[r]; e < A.tr_ptr[r + 1]; ++e) {
+            for (long long e = e0; e < e1; ++e) {
                 const int c = A.tr_col[e];
                 T v;
                 if (MODE == OM_P) v = A.z[c] + beta * A.pold[c];
