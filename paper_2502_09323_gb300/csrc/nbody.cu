@@ -28,6 +28,9 @@ namespace {
 constexpr int NB_THREADS = 256;
 constexpr int NB_TPT = 2;  // targets per thread
 constexpr int NB_GRP = 16; // sources per plainly summed group
+// largest coordinate offset (A) of a block's targets from its first target
+// for the per-block origin form of the differences
+constexpr double NB_ORIGIN_EXT = 8.0;
 
 struct SrcHi {
     float x, y, z, q;
@@ -158,9 +161,17 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 v) {
 
 // The source tiles of one block: per-pair work, group sums and tile sums as
 // described above, accumulated into acc_* (FP64).
-template <bool PSI, bool SCREEN, bool PSI2, int AXIS>
+// ORIGIN: the block's targets lie within NB_ORIGIN_EXT of its first target
+// o, and th holds their positions relative to o as single FP32 values (tl
+// unused); each source is staged once per tile as its FP32 position relative
+// to o, (hi - o_hi) + (lo - o_lo), so that a difference takes one FP32
+// operation instead of three.  Near sources (at least one atom radius away
+// from a point of the molecular surface) then keep about 15 u of relative
+// accuracy in r, far ones about u.
+template <bool PSI, bool SCREEN, bool PSI2, int AXIS, bool ORIGIN>
 __device__ __forceinline__ void nb_tiles(float4 (*sp4)[4], const float4 *__restrict__ shi,
                                          const float4 *__restrict__ slo, long long ns, float kscr,
+                                         const float (&oh)[3], const float (&ol)[3],
                                          const float2 (&th)[3], const float2 (&tl)[3],
                                          const float2 (&tn)[3], const float2 (&tn2)[3],
                                          double (&acc_phi)[NB_TPT], double (&acc_psi)[NB_TPT],
@@ -173,10 +184,17 @@ __device__ __forceinline__ void nb_tiles(float4 (*sp4)[4], const float4 *__restr
             a = shi[si];
             b = slo[si];
         }
-        sp4[threadIdx.x][0] = make_float4(a.x, a.x, a.y, a.y);
-        sp4[threadIdx.x][1] = make_float4(a.z, a.z, a.w, a.w);
-        sp4[threadIdx.x][2] = make_float4(b.x, b.x, b.y, b.y);
-        sp4[threadIdx.x][3] = make_float4(b.z, b.z, 0.f, 0.f);
+        if (ORIGIN) {
+            const float rx = (a.x - oh[0]) + (b.x - ol[0]), ry = (a.y - oh[1]) + (b.y - ol[1]),
+                        rz = (a.z - oh[2]) + (b.z - ol[2]);
+            sp4[threadIdx.x][0] = make_float4(rx, rx, ry, ry);
+            sp4[threadIdx.x][1] = make_float4(rz, rz, a.w, a.w);
+        } else {
+            sp4[threadIdx.x][0] = make_float4(a.x, a.x, a.y, a.y);
+            sp4[threadIdx.x][1] = make_float4(a.z, a.z, a.w, a.w);
+            sp4[threadIdx.x][2] = make_float4(b.x, b.x, b.y, b.y);
+            sp4[threadIdx.x][3] = make_float4(b.z, b.z, 0.f, 0.f);
+        }
         __syncthreads();
         int m = (int)min((long long)NB_THREADS, ns - base);
         float2 sp = bc2(0.f), cp = bc2(0.f), sq = bc2(0.f), cq = bc2(0.f), s2 = bc2(0.f),
@@ -189,13 +207,21 @@ __device__ __forceinline__ void nb_tiles(float4 (*sp4)[4], const float4 *__restr
             float2 gp = bc2(0.f), gq = bc2(0.f), g2 = bc2(0.f);
 #pragma unroll 4
             for (int q = q0; q < q1; ++q) {
-                const float4 p0 = sp4[q][0], p1 = sp4[q][1], p2 = sp4[q][2], p3 = sp4[q][3];
-                const float2 dx = __fadd2_rn(sub2(th[0], make_float2(p0.x, p0.y)),
-                                             sub2(tl[0], make_float2(p2.x, p2.y)));
-                const float2 dy = __fadd2_rn(sub2(th[1], make_float2(p0.z, p0.w)),
-                                             sub2(tl[1], make_float2(p2.z, p2.w)));
-                const float2 dz = __fadd2_rn(sub2(th[2], make_float2(p1.x, p1.y)),
-                                             sub2(tl[2], make_float2(p3.x, p3.y)));
+                const float4 p0 = sp4[q][0], p1 = sp4[q][1];
+                float2 dx, dy, dz;
+                if (ORIGIN) {
+                    dx = sub2(th[0], make_float2(p0.x, p0.y));
+                    dy = sub2(th[1], make_float2(p0.z, p0.w));
+                    dz = sub2(th[2], make_float2(p1.x, p1.y));
+                } else {
+                    const float4 p2 = sp4[q][2], p3 = sp4[q][3];
+                    dx = __fadd2_rn(sub2(th[0], make_float2(p0.x, p0.y)),
+                                    sub2(tl[0], make_float2(p2.x, p2.y)));
+                    dy = __fadd2_rn(sub2(th[1], make_float2(p0.z, p0.w)),
+                                    sub2(tl[1], make_float2(p2.z, p2.w)));
+                    dz = __fadd2_rn(sub2(th[2], make_float2(p1.x, p1.y)),
+                                    sub2(tl[2], make_float2(p3.x, p3.y)));
+                }
                 const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
                 const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f,
                                               r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
@@ -288,23 +314,48 @@ k_nbody(TargetDesc T, const float4 *__restrict__ shi, const float4 *__restrict__
         }
         if (__syncthreads_and(same)) axis = dref;
     }
-    switch (axis) {
-        case 0:
-            nb_tiles<PSI, SCREEN, PSI2, 0>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
-                                           acc_psi, acc_psi2);
-            break;
-        case 1:
-            nb_tiles<PSI, SCREEN, PSI2, 1>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
-                                           acc_psi, acc_psi2);
-            break;
-        case 2:
-            nb_tiles<PSI, SCREEN, PSI2, 2>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
-                                           acc_psi, acc_psi2);
-            break;
-        default:
-            nb_tiles<PSI, SCREEN, PSI2, -1>(sp4, shi, slo, ns, kscr, th, tl, tn, tn2, acc_phi,
-                                            acc_psi, acc_psi2);
+    // a block whose surface targets all lie within NB_ORIGIN_EXT of its
+    // first target takes the differences from that origin
+    bool origin = false;
+    float oh[3] = {0.f, 0.f, 0.f}, ol[3] = {0.f, 0.f, 0.f};
+    if (T.kind == TK_SURFACE) {
+        const long long tb = (long long)blockIdx.x * NB_THREADS * NB_TPT;
+        double o[3], rel[NB_TPT][3];
+        bool near = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) o[d] = T.rp[3 * tb + d];
+#pragma unroll
+        for (int u = 0; u < NB_TPT; ++u) {
+            const long long t = t0 + (long long)u * NB_THREADS;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                rel[u][d] = t < T.count ? T.rp[3 * t + d] - o[d] : 0.0;
+                if (!(fabs(rel[u][d]) <= NB_ORIGIN_EXT)) near = false;
+            }
+        }
+        if (__syncthreads_and(near)) {
+            origin = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double oc = o[d] - T.shift[d];  // the sources are relative to the shift
+                oh[d] = (float)oc;
+                ol[d] = (float)(oc - (double)oh[d]);
+                th[d] = make_float2((float)rel[0][d], (float)rel[1][d]);
+            }
+        }
     }
+#define PB_NB_TILES(AX)                                                                          \
+    (origin ? nb_tiles<PSI, SCREEN, PSI2, AX, true>(sp4, shi, slo, ns, kscr, oh, ol, th, tl, tn, \
+                                                     tn2, acc_phi, acc_psi, acc_psi2)            \
+            : nb_tiles<PSI, SCREEN, PSI2, AX, false>(sp4, shi, slo, ns, kscr, oh, ol, th, tl, tn, \
+                                                      tn2, acc_phi, acc_psi, acc_psi2))
+    switch (axis) {
+        case 0: PB_NB_TILES(0); break;
+        case 1: PB_NB_TILES(1); break;
+        case 2: PB_NB_TILES(2); break;
+        default: PB_NB_TILES(-1);
+    }
+#undef PB_NB_TILES
     if (PSI && axis >= 0) {
         // n = sign e_axis: the one nonzero component is the sign
 #pragma unroll
