@@ -184,6 +184,35 @@ def test_solve_residual_and_energy(pb, case, prec):
         assert abs(e[k] - er[k]) <= 1e-6 * max(abs(er[k]), 1e-3 * abs(er["e_pol"])), k
 
 
+def test_surface_coulomb_terms(pb, O, case, orc):
+    """Phi, Psi along the edge and Psi along the analytic surface normal at
+    the octree's crossing points against the oracle's FP64 sums.  The
+    crossing list in slot order makes the kernel's target blocks compact, so
+    these take the per-block-origin form of the differences (and the axis
+    form of Psi) that the uniform cases mostly do not."""
+    s, tree, ref, atoms = case["s"], case["tree"], case["ref"], case["atoms"]
+    pb.pb_coulomb_terms(s, pb.CT_SURFACE)
+    cr = O.crossing_edges(tree, ref["op"], atoms)
+    flux = cr["sign"] != 0
+    rp = cr["rp"][flux]
+    Phi = pb.pb_get_array(s, "phi_surf")[flux]
+    Psi = pb.pb_get_array(s, "psi_surf")[flux]
+    PsiN = pb.pb_get_array(s, "psi_n")[flux]
+    P_ref = orc.coulomb_phi(rp, atoms)
+    S_ref = orc.coulomb_psi(rp, cr["d"][flux].astype(np.int8), cr["sign"][flux], atoms)
+    N_ref = orc.coulomb_psi_n(rp, cr["mc_n"][flux], atoms)
+    # FP32 error bound: relative to the sum of absolute contributions
+    # (evaluated in chunks of targets to bound the memory of the distances)
+    absq = np.abs(atoms[:, 4])[None, :]
+    for c0 in range(0, len(rp), 8192):
+        sl = slice(c0, c0 + 8192)
+        r = np.linalg.norm(rp[sl, None, :] - atoms[None, :, :3], axis=2)
+        s1, s2 = (absq / r).sum(1), (absq / r ** 2).sum(1)
+        assert np.max(np.abs(Phi[sl] - P_ref[sl]) / s1) <= 2e-6
+        assert np.max(np.abs(Psi[sl] - S_ref[sl]) / s2) <= 2e-6
+        assert np.max(np.abs(PsiN[sl] - N_ref[sl]) / s2) <= 2e-6
+
+
 def test_born_on_octree_gpu(pb, orc):
     atoms = np.array([[0.0, 0.0, 0.0, 2.0, 1.0]])
     g = pb.pb_build_grid(pb.OctreeSpec(h_fine=0.25, h_bulk=1.0, refine_dist=3.0, n0=4,
