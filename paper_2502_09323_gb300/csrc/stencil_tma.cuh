@@ -20,8 +20,8 @@
 // needs from plane k's slot (its row, the rows above and below, the x-edge
 // neighbours, codes) and releases it before it waits for plane k+1, keeping
 // its own row of planes k-1, k, k+1 in registers, so the producer runs up to
-// NSLOT-1 planes ahead of the slowest warp.  No
-// consumer ever waits on another consumer.  Rows without listed edges take
+// NSLOT-1 planes ahead of the slowest warp.  No consumer ever waits on
+// another consumer.  Rows without listed edges take
 // a packed FP32x2 fast path; rows with listed edges gather their weights,
 // issued as soon as the plane's codes are at hand and before the warp waits
 // for the next plane, so the gathers overlap that wait (the update kernel
