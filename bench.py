@@ -347,11 +347,15 @@ def run_batched(args, pb, pb_inputs, torch):
     shapes = {}
     for sp in specs:
         shapes[sp.n[0]] = shapes.get(sp.n[0], 0) + 1
+    # the autotuner's tile width and z-chunk per grid shape
+    tiles = {str(sp.n[0]): {"tile_width": x["kc"] // 10000, "z_chunk": x["kc"] % 1000}
+             for sp, x in zip(specs, st)}
     out = {
         "workload": f"{count} globular molecules, atoms log-uniform [200, 3000] (seed 4000 + i), "
                     f"uniform grids h = 0.5 A, n in {list(BATCH_SIZES)}, fill 1.5, eps 2/80, "
                     "0.145 M, zero BC, rtol 1e-8",
         "grids": {str(k): v for k, v in sorted(shapes.items())},
+        "tuned_tiles": dict(sorted(tiles.items(), key=lambda kv: int(kv[0]))),
         "solves_per_s": count / t_mixed, "seconds": t_mixed,
         "fp64_plain_solves_per_s": count / t64, "fp64_seconds": t64,
         "speedup_mixed_over_fp64": t64 / t_mixed,
@@ -829,6 +833,7 @@ def run_ours(args, wl):
                            if stats[-1]["kc"] >= 1000 else
                            "k_stencil<float,CoefC32,MODE_U> (FP32 PCG update)"),
                 "z_chunk": stats[-1]["kc"] % 1000,
+                "tile_width": stats[-1]["kc"] // 10000 or None,
                 "alg_bytes_per_launch": bytes_u, "launch_s": kt["update"],
                 "peak_kind": f"{peak_kind} hbm_gbs",
                 "direction_kernel": {"launch_s": kt["direction"],

@@ -150,7 +150,8 @@ typedef struct {
     int32_t status;           /* pb_status of the solve                     */
     int32_t iters_inner;      /* PCG iterations (FP32 inner or FP64 plain)  */
     int32_t iters_outer;      /* FP64 residual evaluations                  */
-    int32_t kc;               /* tuned kernel: z-chunk + 1000 * variant     */
+    int32_t kc;               /* tuned kernel: z-chunk + 1000 * variant
+                                 (+ 10000 * tile width, TMA-staged variant) */
     double true_rel_res;      /* ||f - A phi|| / ||f|| in FP64 at exit      */
     double seconds;           /* host wall time of the call                 */
     int64_t dof;              /* interior unknowns                          */
@@ -377,7 +378,10 @@ pb_status pb_profile_kernels(pb_system *s, int32_t precision, int32_t which, int
 /* pb_set_tuning -- fix the PCG kernel variant (0: register-pipelined warps,
  * 1: TMA-staged, FP32 only) and z-chunk length (planes per block) used for
  * every system with s's grid shape and this precision, instead of the
- * autotuner's choice (which times the candidates on first use of a shape). */
+ * autotuner's choice (which times the candidates on first use of a shape).
+ * For the TMA-staged variant z_chunk may add 10000 * the tile width in x
+ * (128, 64 or 32 points; tiles are width x 1024/width points of a plane;
+ * no addition: 128).  Other widths give PB_ERR_ARG. */
 pb_status pb_set_tuning(pb_system *s, int32_t precision, int32_t variant, int32_t z_chunk);
 
 /* pb_solve_split -- the mixed-precision solve of pb_solve (uniform grids) on

@@ -435,6 +435,9 @@ def pb_profile_kernels(system: System, precision: int, which: int, reps: int, st
 
 
 def pb_set_tuning(system: System, precision: int, variant: int, z_chunk: int) -> None:
+    """Fix the PCG kernel variant and z-chunk for the system's grid shape;
+    for the TMA-staged variant z_chunk may add 10000 x the tile width (128,
+    64 or 32)."""
     N.check(N.lib().pb_set_tuning(system.handle, int(precision), int(variant), int(z_chunk)))
 
 

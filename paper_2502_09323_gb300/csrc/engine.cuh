@@ -115,6 +115,7 @@ struct EngineJob {
     long long ticket = 0;
     cudaEvent_t ready = nullptr;  // recorded on the submitting stream
     int kc = 8;
+    int tw = tma::TWDEF;          // tile width of the TMA-staged kernels
     bool oct = false;             // octree system: brick kernels beside the table
     long long dof = 0;
     double t_submit = 0.0;
@@ -246,8 +247,11 @@ bool engine_upload_table(Engine *e) {
         tma::SysEntry &en = h[q];
         const HostSlot &hs = e->slots[q];
         if (hs.used && !hs.job.oct) {
-            en = ((TmaState *)hs.job.sys->tma)->host;
-            tma_entry_geometry(en, hs.job.sys->pad, hs.job.kc);
+            const TmaState *ts = (const TmaState *)hs.job.sys->tma;
+            en = ts->host;
+            // the tile width of the maps the entry holds (the job's, set at
+            // submission)
+            tma_entry_geometry(en, hs.job.sys->pad, hs.job.kc, ts->tw);
         } else {  // free slot, or an octree system (solved beside the table)
             memset(&en, 0, sizeof(en));
             en.nitems = 0;
@@ -284,7 +288,7 @@ void engine_complete(Engine *e, int q, const EngineSlot &m) {
     r.stats.status = m.ctl.status;
     r.stats.iters_inner = m.ctl.iters;
     r.stats.iters_outer = m.ctl.outer;
-    r.stats.kc = hs.job.oct ? 0 : hs.job.kc + 1000;
+    r.stats.kc = hs.job.oct ? 0 : hs.job.kc + 1000 + 10000 * hs.job.tw;
     r.stats.true_rel_res = m.ctl.fn2 > 0.0 ? sqrt(m.ctl.res2 / m.ctl.fn2) : 0.0;
     r.stats.dof = hs.job.dof;
     r.stats.model_bytes = (long long)m.ctl.iters * r.stats.dof * (8 * 4 + 2) +
@@ -530,6 +534,9 @@ pb_status engine_submit(pb_engine *eh, pb_system *sys, cudaStream_t s, long long
         Tuning tune;
         if ((rc = autotune(sys, PB_MIXED, s, &tune)) != PB_OK) return rc;
         j.kc = tune.variant == 1 ? std::max(tune.kc, 4) : 8;
+        j.tw = tune.variant == 1 ? tune.tw : tma::TWDEF;
+        // the entry the table copies holds the maps of this tile width
+        if ((rc = tma_set_tile(sys, j.tw)) != PB_OK) return rc;
         const GridGeo &gg = sys->g->geo;
         j.dof = (long long)(gg.nx - 2) * (gg.ny - 2) * (gg.nz - 2);
     }

@@ -705,15 +705,16 @@ pb_status make_map(CUtensorMap *m, const void *base, bool bytes, const PadGeo &g
     return PB_OK;
 }
 
-// maps of one TMA stencil launch
+// maps of one TMA stencil launch with tiles of width tw
 pb_status tma_maps(const pb_system *sys, int mode, const float *a, const float *b, const float *x,
-                   const float *z, tma::Maps *m) {
+                   const float *z, tma::Maps *m, int tw) {
     const PadGeo &g = sys->pad;
-    pb_status rc = make_map(&m->a, a, false, g, tma::BOXW, tma::BOXH);
-    if (rc == PB_OK && mode == MODE_P) rc = make_map(&m->b, b, false, g, tma::BOXW, tma::BOXH);
-    if (rc == PB_OK && mode == MODE_U) rc = make_map(&m->x, x, false, g, tma::OWNW, tma::ROWS);
-    if (rc == PB_OK && mode == MODE_U) rc = make_map(&m->z, z, false, g, tma::OWNW, tma::ROWS);
-    if (rc == PB_OK) rc = make_map(&m->code, sys->code, true, g, tma::CODEW, tma::BOXH);
+    const int bw = tma::box_w(tw), bh = tma::box_h(tw), th = tma::tile_h(tw);
+    pb_status rc = make_map(&m->a, a, false, g, bw, bh);
+    if (rc == PB_OK && mode == MODE_P) rc = make_map(&m->b, b, false, g, bw, bh);
+    if (rc == PB_OK && mode == MODE_U) rc = make_map(&m->x, x, false, g, tw, th);
+    if (rc == PB_OK && mode == MODE_U) rc = make_map(&m->z, z, false, g, tw, th);
+    if (rc == PB_OK) rc = make_map(&m->code, sys->code, true, g, tma::code_w(tw), bh);
     return rc;
 }
 
@@ -790,22 +791,36 @@ struct TmaState {
     tma::SysEntry *dev = nullptr;  // device copy (a table of one)
     float *partials = nullptr;   // per-item dot-product slots
     unsigned int *cnt = nullptr;
-    int uploaded_kc = -1;
+    int tw = tma::TWDEF;         // tile width of the maps in host
+    int uploaded_kc = -1, uploaded_tw = -1;
     int max_items = 0;
 };
 
-int tma_items(const PadGeo &g, int KC) {
-    return (int)(cdiv(g.nx - 1, tma::OWNW) * cdiv(g.ny - 2, tma::ROWS) * cdiv(g.nz - 2, KC));
+int tma_items(const PadGeo &g, int KC, int tw) {
+    return (int)(cdiv(g.nx - 1, tw) * cdiv(g.ny - 2, tma::tile_h(tw)) * cdiv(g.nz - 2, KC));
 }
 
-// entry fields that depend on the z-chunk length
-void tma_entry_geometry(tma::SysEntry &e, const PadGeo &g, int KC) {
-    e.xtiles = (int)cdiv(g.nx - 1, tma::OWNW);
-    e.ytiles = (int)cdiv(g.ny - 2, tma::ROWS);
+// entry fields that depend on the z-chunk length and the tile width
+void tma_entry_geometry(tma::SysEntry &e, const PadGeo &g, int KC, int tw) {
+    e.tw = tw;
+    e.xtiles = (int)cdiv(g.nx - 1, tw);
+    e.ytiles = (int)cdiv(g.ny - 2, tma::tile_h(tw));
     e.KC = KC;
     e.nchunk = (int)cdiv(g.nz - 2, KC);
     e.nitems = e.xtiles * e.ytiles * e.nchunk;
     e.item_base = 0;
+}
+
+// the direction and update maps of a system's entry for tiles of width tw
+pb_status tma_sys_maps(pb_system *sys, tma::SysEntry &e, int tw) {
+    const float *pbuf[2] = {sys->pa32, sys->pb32};
+    pb_status rc = PB_OK;
+    for (int c = 0; c < 2 && rc == PB_OK; ++c) {
+        rc = tma_maps(sys, MODE_P, sys->z32, pbuf[c], nullptr, nullptr, &e.P[c], tw);
+        if (rc == PB_OK)
+            rc = tma_maps(sys, MODE_U, pbuf[c ^ 1], nullptr, sys->d32, sys->z32, &e.U[c], tw);
+    }
+    return rc;
 }
 
 CoefC32 make_c32(const pb_system *sys);
@@ -817,11 +832,8 @@ pb_status build_tma_state(pb_system *sys) {
     cudaStream_t s = sys->stream;
     pb_status rc = PB_OK;
     tma::SysEntry &e = t->host;
-    const float *pbuf[2] = {sys->pa32, sys->pb32};
-    for (int c = 0; c < 2 && rc == PB_OK; ++c) {
-        rc = tma_maps(sys, MODE_P, sys->z32, pbuf[c], nullptr, nullptr, &e.P[c]);
-        if (rc == PB_OK) rc = tma_maps(sys, MODE_U, pbuf[c ^ 1], nullptr, sys->d32, sys->z32, &e.U[c]);
-    }
+    rc = tma_sys_maps(sys, e, t->tw);
+    e.tw = t->tw;
     if (rc == PB_OK) rc = tma_prepare<MODE_P>();
     if (rc == PB_OK) rc = tma_prepare<MODE_U>();
     if (rc == PB_OK) rc = tma_prepare<MODE_A>();
@@ -833,7 +845,8 @@ pb_status build_tma_state(pb_system *sys) {
     e.z = sys->z32;
     e.y = nullptr;
     e.st = sys->st;
-    t->max_items = tma_items(sys->pad, 4);
+    t->max_items = std::max(tma_items(sys->pad, 4, 128),
+                            std::max(tma_items(sys->pad, 4, 64), tma_items(sys->pad, 4, 32)));
     if (rc == PB_OK) {
         t->dev = (tma::SysEntry *)dalloc(sizeof(tma::SysEntry), s);
         t->partials = (float *)dalloc(sizeof(float) * 3 * (size_t)t->max_items, s);
@@ -855,25 +868,43 @@ pb_status build_tma_state(pb_system *sys) {
     return PB_OK;
 }
 
-// make the device entry describe z-chunks of KC planes (KC >= 4)
-pb_status tma_use_kc(pb_system *sys, int KC, cudaStream_t s) {
+// make the host entry's maps those of tiles of width tw (host only)
+pb_status tma_set_tile(pb_system *sys, int tw) {
+    TmaState *t = (TmaState *)sys->tma;
+    if (t->tw == tw) return PB_OK;
+    pb_status rc = tma_sys_maps(sys, t->host, tw);
+    if (rc != PB_OK) return rc;
+    t->tw = tw;
+    t->host.tw = tw;
+    t->uploaded_kc = -1;
+    return PB_OK;
+}
+
+// make the device entry describe z-chunks of KC planes (KC >= 4) of tiles
+// of width tw
+pb_status tma_use_kc(pb_system *sys, int KC, int tw, cudaStream_t s) {
     TmaState *t = (TmaState *)sys->tma;
     if (KC < 4) KC = 4;
-    if (t->uploaded_kc == KC) return PB_OK;
-    tma_entry_geometry(t->host, sys->pad, KC);
+    pb_status rc = tma_set_tile(sys, tw);
+    if (rc != PB_OK) return rc;
+    if (t->uploaded_kc == KC && t->uploaded_tw == tw) return PB_OK;
+    tma_entry_geometry(t->host, sys->pad, KC, tw);
     PB_CUDA_TRY(cudaMemcpyAsync(t->dev, &t->host, sizeof(tma::SysEntry), cudaMemcpyHostToDevice, s));
     // the host copy must not change before the copy has been made
     PB_CUDA_TRY(cudaStreamSynchronize(s));
     t->uploaded_kc = KC;
+    t->uploaded_tw = tw;
     return PB_OK;
 }
 
 // one FP32 PCG iteration (direction + update kernels) with TMA staging;
-// cur selects which of pa/pb holds p_old
-void launch_iter_tma(pb_system *sys, const CoefC32 &, int cur, int KC, cudaStream_t s) {
+// cur selects which of pa/pb holds p_old; blocks > 0 sets the grid size
+// (timing runs), else one block per resident slot
+void launch_iter_tma(pb_system *sys, const CoefC32 &, int cur, int KC, int tw, cudaStream_t s,
+                     unsigned blocks = 0) {
     TmaState *t = (TmaState *)sys->tma;
-    if (tma_use_kc(sys, KC, s) != PB_OK) return;
-    dim3 grid = tma_grid(sys->pad, KC);
+    if (tma_use_kc(sys, KC, tw, s) != PB_OK) return;
+    dim3 grid = blocks ? dim3(blocks) : tma_grid(sys->pad, KC);
     tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
     tma_launch<MODE_U>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
 }
@@ -1015,7 +1046,7 @@ pb_status residual(pb_system *sys, bool fp32_out, cudaStream_t s) {
 // copy of the state after every chunk, keeping two chunks in flight.
 template <typename T, class CP>
 pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC, int variant,
-                  int chunk,
+                  int tw, int chunk,
                   double deadline, cudaStream_t s, int *iters_out) {
     T *bufs[2] = {pa, pb};
     int cur = 0;  // index of p_old
@@ -1028,7 +1059,7 @@ pb_status run_pcg(pb_system *sys, const CP &cp, T *z, T *pa, T *pb, T *x, int KC
         for (int c = 0; c < chunk; ++c) {
             if constexpr (std::is_same<T, float>::value) {
                 if (variant == 1)
-                    launch_iter_tma(sys, cp, cur, KC, s);
+                    launch_iter_tma(sys, cp, cur, KC, tw, s);
                 else
                     launch_iter<T, CP>(sys, cp, z, bufs[cur], bufs[cur ^ 1], x, z, KC, s);
             } else {
@@ -1113,23 +1144,26 @@ pb_status init_state(pb_system *sys, double rho, double rr0, double rr_stop, int
 }
 
 // ---------------------------------------------------------------- tuner --
-// Kernel variant (0: register-pipelined warps, 1: TMA-staged, FP32 only)
-// and z-chunk length chosen by timing one PCG iteration of each candidate on
-// the system itself; cached per (precision, grid shape).
+// Kernel variant (0: register-pipelined warps, 1: TMA-staged, FP32 only),
+// z-chunk length and (TMA-staged) tile width chosen by timing PCG iterations
+// of each candidate on the system itself; cached per (precision, grid shape).
 struct Tuning {
     int variant = 0;
     int kc = 8;
+    int tw = tma::TWDEF;
 };
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, Tuning> g_tune;
 
-// one PCG iteration of the given kernel variant and z-chunk (timing runs)
-void tune_iter(pb_system *sys, int precision, int variant, int kc, int r, cudaStream_t s) {
+// one PCG iteration of the given kernel variant, z-chunk and tile width
+// (timing runs; blocks > 0: the TMA-staged kernels on that many blocks)
+void tune_iter(pb_system *sys, int precision, int variant, int kc, int tw, int r, cudaStream_t s,
+               unsigned blocks = 0) {
     if (precision == PB_MIXED) {
         CoefC32 cp = make_c32(sys);
         if (variant == 1)
-            launch_iter_tma(sys, cp, r & 1, kc, s);
+            launch_iter_tma(sys, cp, r & 1, kc, tw, s, blocks);
         else
             launch_iter<float, CoefC32>(sys, cp, sys->z32, (r & 1) ? sys->pb32 : sys->pa32,
                                         (r & 1) ? sys->pa32 : sys->pb32, sys->d32, sys->z32, kc, s);
@@ -1139,17 +1173,18 @@ void tune_iter(pb_system *sys, int precision, int variant, int kc, int r, cudaSt
     note_launch(2);
 }
 
-// time of two PCG iterations with z-chunk kc (after one untimed iteration,
-// which also absorbs the switch of the launch-table entry to kc)
-pb_status time_candidate(pb_system *sys, int precision, int variant, int kc, cudaStream_t s,
-                         float *ms) {
+// time of two PCG iterations with z-chunk kc and tile width tw (after one
+// untimed iteration, which also absorbs the switch of the launch-table entry);
+// blocks > 0: the TMA-staged kernels on that many blocks
+pb_status time_candidate(pb_system *sys, int precision, int variant, int kc, int tw,
+                         cudaStream_t s, float *ms, unsigned blocks = 0) {
     cudaEvent_t ev[2];
     PB_CUDA_TRY(cudaEventCreate(&ev[0]));
     PB_CUDA_TRY(cudaEventCreate(&ev[1]));
-    tune_iter(sys, precision, variant, kc, 0, s);
+    tune_iter(sys, precision, variant, kc, tw, 0, s, blocks);
     PB_CUDA_TRY(cudaEventRecord(ev[0], s));
-    tune_iter(sys, precision, variant, kc, 1, s);
-    tune_iter(sys, precision, variant, kc, 2, s);
+    tune_iter(sys, precision, variant, kc, tw, 1, s, blocks);
+    tune_iter(sys, precision, variant, kc, tw, 2, s, blocks);
     PB_CUDA_TRY(cudaEventRecord(ev[1], s));
     PB_CUDA_TRY(cudaEventSynchronize(ev[1]));
     PB_CUDA_TRY(cudaGetLastError());
@@ -1178,32 +1213,77 @@ pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
     if (rc != PB_OK) return rc;
     // mixed precision always runs the TMA-staged kernels (the batched solver
     // shares them, so a system gives the same bits alone and in a batch);
-    // only their z-chunk is tuned.  FP64 runs the register-pipelined kernels.
+    // their z-chunk and tile width are tuned.  FP64 runs the
+    // register-pipelined kernels, whose z-chunk is tuned.
     const int variant = precision == PB_MIXED ? 1 : 0;
     Tuning best;
     best.variant = variant;
     const int kcs[] = {8, 6, 11, 16, 22, 32};  // first = default
-    // a persistent launch balances its work queue only with a few items per
-    // block: longer chunks that leave fewer are not candidates
-    const long long blocks = variant == 1 ? (long long)tma_grid(g, 8).x : 0;
-    const long long floor_items = variant == 1 ? std::min<long long>(tma_items(g, kcs[0]), 4 * blocks) : 0;
-    std::vector<int> cand;
-    for (int kc : kcs) {
-        if (kc != kcs[0] && kc > g.nz - 2) continue;
-        if (variant == 1 && kc != kcs[0] && tma_items(g, kc) < floor_items) continue;
-        cand.push_back(kc);
+    // tile widths: those whose tiles cover the interior of a plane with the
+    // fewest idle lanes (smallest padded area), widest first.  A small grid
+    // timed alone cannot fill the GPU, so its timings would not show the idle
+    // lanes it costs when it shares launches with other systems (a 97-node
+    // grid leaves a quarter of a 128-wide tile idle); the widths that tie are
+    // timed.
+    std::vector<int> tws = {tma::TWDEF};
+    if (variant == 1) {
+        auto area = [&](int tw) {
+            return cdiv(g.nx - 1, tw) * tw * cdiv(g.ny - 2, tma::tile_h(tw)) * tma::tile_h(tw);
+        };
+        const long long amin = std::min(area(128), std::min(area(64), area(32)));
+        tws.clear();
+        for (int tw : {128, 64, 32})
+            if (area(tw) == amin) tws.push_back(tw);
+        best.tw = tws[0];
     }
+    // A persistent launch balances its work queue only with a few items per
+    // block: on a grid that fills the GPU alone, longer chunks that leave
+    // fewer are not candidates.  A grid too small for that (fewer than four
+    // items per resident block at the default chunk) shares its launches
+    // with other systems when it is batched or served; its candidates are
+    // timed on about a quarter as many blocks as they have items and ranked
+    // by block-time (time x blocks), the share of a full launch they take.
+    const long long blocks = variant == 1 ? (long long)tma_grid(g, 8).x : 0;
+    const bool shared = variant == 1 && tma_items(g, kcs[0], tws[0]) < 4 * blocks;
+    std::vector<std::pair<int, int>> cand;  // (tile width, z-chunk)
+    for (int tw : tws) {
+        const long long floor_items =
+            variant == 1 ? std::min<long long>(tma_items(g, kcs[0], tw), 4 * blocks) : 0;
+        for (int kc : kcs) {
+            if (kc != kcs[0] && kc > g.nz - 2) continue;
+            if (variant == 1 && !shared && kc != kcs[0] && tma_items(g, kc, tw) < floor_items)
+                continue;
+            cand.push_back({tw, kc});
+        }
+    }
+    auto cand_blocks = [&](const std::pair<int, int> &c) -> unsigned {
+        if (!shared) return 0u;
+        const long long b = cdiv(tma_items(g, std::max(c.second, 4), c.first), 4);
+        return (unsigned)std::max(1ll, std::min(b, blocks));
+    };
     // clocks and caches to steady state, then round-robin timings (drift
     // during tuning then affects every candidate alike); median per candidate
-    for (int i = 0; i < 12; ++i) tune_iter(sys, precision, variant, kcs[0], i, s);
+    for (int i = 0; i < 12; ++i) tune_iter(sys, precision, variant, kcs[0], tws[0], i, s);
     const int rounds = 3;
     std::vector<std::vector<float>> t(cand.size());
     for (int r = 0; r < rounds; ++r)
         for (size_t c = 0; c < cand.size(); ++c) {
             float ms = 0.f;
-            if ((rc = time_candidate(sys, precision, variant, cand[c], s, &ms)) != PB_OK) return rc;
-            t[c].push_back(ms);
+            const unsigned nb = cand_blocks(cand[c]);
+            if ((rc = time_candidate(sys, precision, variant, cand[c].second, cand[c].first, s,
+                                     &ms, nb)) != PB_OK)
+                return rc;
+            t[c].push_back(shared ? ms * (float)nb : ms);
         }
+    if (variant == 1) {
+        // The timing runs never stop and leave arbitrary values (NaN after a
+        // breakdown) in the FP32 vectors, also at the points past a row's
+        // last tile that a wider candidate wrote and a narrower tile never
+        // rewrites (the boundary column among them): clear them all.
+        const size_t b32 = sizeof(float) * (size_t)g.Np;
+        for (float *v : {sys->z32, sys->pa32, sys->pb32, sys->d32})
+            PB_CUDA_TRY(cudaMemsetAsync(v, 0, b32, s));
+    }
     float best_ms = 1e30f;
     for (size_t c = 0; c < cand.size(); ++c) {
         std::sort(t[c].begin(), t[c].end());
@@ -1212,7 +1292,8 @@ pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
         // otherwise make the choice, and the dot-product partition, vary)
         if (ms < 0.97f * best_ms) {
             best_ms = ms;
-            best.kc = cand[c];
+            best.tw = cand[c].first;
+            best.kc = cand[c].second;
         }
     }
     {
@@ -1226,9 +1307,12 @@ pb_status autotune(pb_system *sys, int precision, cudaStream_t s, Tuning *out) {
 }  // namespace
 
 pb_status set_tuning(pb_system *sys, int precision, int variant, int kc) {
-    if (kc < 1 || variant < 0 || variant > 1 ||
+    // kc = z-chunk + 10000 * tile width (0: the default width)
+    const int tw = kc / 10000 ? kc / 10000 : tma::TWDEF;
+    kc %= 10000;
+    if (kc < 1 || variant < 0 || variant > 1 || !tma::tile_ok(tw) ||
         (variant == 1 && precision != PB_MIXED)) {
-        set_error("bad tuning (variant %d, z-chunk %d)", variant, kc);
+        set_error("bad tuning (variant %d, z-chunk %d, tile width %d)", variant, kc, tw);
         return PB_ERR_ARG;
     }
     const PadGeo &g = sys->pad;
@@ -1236,6 +1320,7 @@ pb_status set_tuning(pb_system *sys, int precision, int variant, int kc) {
     Tuning t;
     t.variant = variant;
     t.kc = kc;
+    t.tw = tw;
     g_tune[std::make_tuple(precision, g.nx, g.ny, g.nz)] = t;
     return PB_OK;
 }
@@ -1361,7 +1446,7 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
             PB_CUDA_TRY(cudaMemsetAsync(sys->pa32, 0, bytes32, s));
             int it = 0;
             rc = run_pcg<float, CoefC32>(sys, cp, sys->z32, sys->pa32, sys->pb32, sys->d32, tune.kc,
-                                         tune.variant, chunk, deadline, s, &it);
+                                         tune.variant, tune.tw, chunk, deadline, s, &it);
             if (rc == PB_OK && sys->h_st[0].status == 3) {
                 // the correction of an aborted inner solve is incomplete: it
                 // is not promoted, phi keeps the last refined iterate
@@ -1414,7 +1499,7 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
             PB_CUDA_TRY(cudaMemsetAsync(sys->pa64, 0, bytes64, s));
             int it = 0;
             rc = run_pcg<double, CoefS64>(sys, cp, sys->z64, sys->pa64, sys->pb64, sys->x64, tune.kc,
-                                          0, chunk, deadline, s, &it);
+                                          0, tma::TWDEF, chunk, deadline, s, &it);
             if (rc == PB_ERR_TIMEOUT) status = PB_ERR_TIMEOUT;
             else if (rc != PB_OK) return rc;
             if (rc == PB_OK) iters += it;
@@ -1435,7 +1520,7 @@ pb_status solve(pb_system *sys, const pb_solve_opts *o, cudaStream_t s, pb_solve
         stats->status = status;
         stats->iters_inner = iters;
         stats->iters_outer = outer;
-        stats->kc = tune.kc + 1000 * tune.variant;
+        stats->kc = tune.kc + 1000 * tune.variant + (tune.variant == 1 ? 10000 * tune.tw : 0);
         stats->true_rel_res = fn2 > 0.0 ? sqrt(res2 / fn2) : 0.0;
         stats->seconds = now_s() - t_start;
         stats->dof = (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2);
@@ -1476,7 +1561,7 @@ pb_status profile_kernels(pb_system *sys, int precision, int which, int reps, cu
         const int cur = r & 1;
         if (precision == PB_MIXED && tune.variant == 1) {
             TmaState *t = (TmaState *)sys->tma;
-            if ((rc = tma_use_kc(sys, KC, s)) != PB_OK) return rc;
+            if ((rc = tma_use_kc(sys, KC, tune.tw, s)) != PB_OK) return rc;
             dim3 grid = tma_grid(sys->pad, KC);
             if (which == 0 || which == 2) {
                 tma_launch<MODE_P>(t->dev, 1, t->host.nitems, sys->queue, grid, s, &t->host, true);
@@ -1538,7 +1623,8 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
         // a one-entry table of its own (the solver's entry may be in use)
         tma::SysEntry *e = new (std::nothrow) tma::SysEntry();
         if (!e) return PB_ERR_OOM;
-        pb_status rc = tma_maps(sys, MODE_A, (const float *)xp, nullptr, nullptr, nullptr, &e->A);
+        pb_status rc =
+            tma_maps(sys, MODE_A, (const float *)xp, nullptr, nullptr, nullptr, &e->A, tma::TWDEF);
         if (rc == PB_OK) rc = tma_prepare<MODE_A>();
         if (rc != PB_OK) {
             delete e;
@@ -1547,7 +1633,7 @@ pb_status apply_op(pb_system *sys, int precision, const void *x, void *y, cudaSt
         e->pg = p;
         e->cp = make_c32(sys);
         e->y = (float *)yp;
-        tma_entry_geometry(*e, p, 8);
+        tma_entry_geometry(*e, p, 8, tma::TWDEF);
         tma::SysEntry *de = (tma::SysEntry *)dalloc(sizeof(tma::SysEntry), s);
         if (!de) {
             delete e;

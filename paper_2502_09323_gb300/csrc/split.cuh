@@ -122,7 +122,7 @@ pb_status copy_planes(void *dst, const void *src, long long g0, long long n, lon
     return PB_OK;
 }
 
-pb_status slab_build(const pb_system *sys, Slab &sl, int k0, int k1, int KC, int dev,
+pb_status slab_build(const pb_system *sys, Slab &sl, int k0, int k1, int KC, int tw, int dev,
                      cudaStream_t s) {
     const GridGeo &G = sys->g->geo;
     const PadGeo &P = sys->pad;
@@ -153,7 +153,7 @@ pb_status slab_build(const pb_system *sys, Slab &sl, int k0, int k1, int KC, int
     sl.npartials = (int)(2 * cdiv(cN, 256) + 64);
     sl.partials = (double *)dalloc(8 * (size_t)sl.npartials, s);
     sl.queue = (unsigned int *)dalloc(4 * sizeof(unsigned int), s);
-    const int nitems = tma_items(sl.pg, KC);
+    const int nitems = tma_items(sl.pg, KC, tw);
     sl.tpart = (float *)dalloc(sizeof(float) * 3 * (size_t)nitems, s);
     sl.dev = (tma::SysEntry *)dalloc(sizeof(tma::SysEntry), s);
     if (!sl.W[0] || !sl.W[1] || !sl.W[2] || !sl.w32[0] || !sl.w32[1] || !sl.w32[2] || !sl.diag ||
@@ -181,8 +181,9 @@ pb_status slab_build(const pb_system *sys, Slab &sl, int k0, int k1, int KC, int
         pb_system view{};
         view.pad = sl.pg;
         view.code = sl.code;
-        rc = tma_maps(&view, MODE_P, sl.z, sl.pbuf[c], nullptr, nullptr, &e.P[c]);
-        if (rc == PB_OK) rc = tma_maps(&view, MODE_U, sl.pbuf[c ^ 1], nullptr, sl.d, sl.z, &e.U[c]);
+        rc = tma_maps(&view, MODE_P, sl.z, sl.pbuf[c], nullptr, nullptr, &e.P[c], tw);
+        if (rc == PB_OK)
+            rc = tma_maps(&view, MODE_U, sl.pbuf[c ^ 1], nullptr, sl.d, sl.z, &e.U[c], tw);
     }
     if (rc != PB_OK) return rc;
     e.pg = sl.pg;
@@ -198,7 +199,7 @@ pb_status slab_build(const pb_system *sys, Slab &sl, int k0, int k1, int KC, int
     e.st = sl.st;
     e.partials = sl.tpart;
     e.cnt = nullptr;
-    tma_entry_geometry(e, sl.pg, KC);
+    tma_entry_geometry(e, sl.pg, KC, tw);
     PB_CUDA_TRY(cudaMemcpyAsync(sl.dev, &e, sizeof(e), cudaMemcpyHostToDevice, s));
     (void)dev;
     return PB_OK;
@@ -298,7 +299,7 @@ pb_status solve_split(pb_system *sys, int R, const pb_solve_opts *o, cudaStream_
     if ((rc = build_tma_state(sys)) != PB_OK) return rc;
     Tuning tune;
     if ((rc = autotune(sys, PB_MIXED, s, &tune)) != PB_OK) return rc;
-    const int KC = std::max(tune.kc, 4);
+    const int KC = std::max(tune.kc, 4), TW = tune.tw;
     const int max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     const double rtol = o->rtol > 0.0 ? o->rtol : 1e-8;
@@ -313,7 +314,7 @@ pb_status solve_split(pb_system *sys, int R, const pb_solve_opts *o, cudaStream_
         for (int r = 0; r < R && rc == PB_OK; ++r) {
             const int k0 = 1 + (int)((long long)nint * r / R);
             const int k1 = 1 + (int)((long long)nint * (r + 1) / R);
-            rc = slab_build(sys, sl[r], k0, k1, KC, dev, s);
+            rc = slab_build(sys, sl[r], k0, k1, KC, TW, dev, s);
         }
         if (rc != PB_OK) break;
         dsts = (CgState **)dalloc(sizeof(CgState *) * R, s);
@@ -427,7 +428,7 @@ pb_status solve_split(pb_system *sys, int R, const pb_solve_opts *o, cudaStream_
         stats->status = status;
         stats->iters_inner = iters;
         stats->iters_outer = outer;
-        stats->kc = KC + 1000;
+        stats->kc = KC + 1000 + 10000 * TW;
         stats->true_rel_res = fn2 > 0.0 ? sqrt(res2 / fn2) : 0.0;
         stats->seconds = now_s() - t_start;
         stats->dof = (long long)(G.nx - 2) * (G.ny - 2) * (G.nz - 2);

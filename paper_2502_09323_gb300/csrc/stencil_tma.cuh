@@ -3,20 +3,22 @@
 // One launch serves every system of a table (a single solve is a table of
 // one; a batch of uneven solves is a table of many).  Blocks are resident for
 // the whole launch and pull work items -- z-chunks of KC planes of one
-// 128 x 8 tile column of one system -- from a global atomic counter.  The
+// TW x (1024 / TW) tile column of one system (TW = 128, 64 or 32 per grid
+// shape) -- from a global atomic counter.  The
 // producer announces each chunk in a small descriptor ring before arming the
 // chunk's first plane, so consumers learn it through the same mbarrier; the
 // TMA pipeline keeps streaming across chunks and systems.
 //
 // One producer warp (lane 0) issues, for every plane, tensor-map
 // (cp.async.bulk.tensor) loads of
-//   * the streamed vector on a 136 x 10 box (4 columns of x halo on each side
-//     and one halo row above and below; out-of-range elements are zero),
-//   * for the update kernel, the x and z rows of the tile (128 x 8),
-//   * the code bytes on a 160 x 10 box,
+//   * the streamed vector on a (TW + 8) x (TH + 2) box (4 columns of x halo
+//     on each side and one halo row above and below; out-of-range elements
+//     are zero), 136 x 10 for the 128 x 8 tile,
+//   * for the update kernel, the x and z rows of the tile (TW x TH),
+//   * the code bytes on a (TW + 32) x (TH + 2) box,
 // into a ring of NSLOT shared-memory slots, each guarded by a "full" mbarrier
 // (transaction bytes) and an "empty" mbarrier (one arrival per consumer warp).
-// The 8 consumer warps compute one row each; a warp reads everything it
+// The 8 consumer warps compute TH / 8 rows each; a warp reads everything it
 // needs from plane k's slot (its row, the rows above and below, the x-edge
 // neighbours, codes) and releases it before it waits for plane k+1, keeping
 // its own row of planes k-1, k, k+1 in registers, so the producer runs up to
@@ -46,22 +48,37 @@
 
 namespace tma {
 
-constexpr int ROWS = 8;              // consumer warps = tile rows
+constexpr int ROWS = 8;              // consumer warps
 constexpr int NSLOT = 6;             // ring depth
-constexpr int BOXW = 136;            // streamed box width (floats), x from i0-4
-constexpr int OWNW = 128;            // own-row box width (floats), x from i0
-constexpr int CODEW = 160;           // code box width (bytes), x from i0-16
-constexpr int BOXH = ROWS + 2;       // rows j0-1 .. j0+ROWS
 constexpr int NTHREADS = 32 * (ROWS + 1);
+// A tile is TW x (1024 / TW) points of one plane (TW = 128, 64 or 32, chosen
+// per grid shape): warp w owns tile rows w * RPW .. w * RPW + RPW - 1
+// (RPW = 32 / TW * 4 rows per warp), TW / 4 lanes per row, 4 points a lane.
+// Narrow tiles fit grids whose interior is not a multiple of 128 points
+// across (97- or 161-node grids leave a quarter or three eighths of a
+// 128-wide tile idle).  Boxes per plane:
+//   streamed vector (TW + 8) x (TH + 2), x from i0 - 4, rows j0 - 1 .. j0 + TH
+//   own rows        TW x TH, x from i0
+//   code bytes      (TW + 32) x (TH + 2), x from i0 - 16
+__host__ __device__ constexpr int tile_h(int tw) { return 1024 / tw; }
+__host__ __device__ constexpr int box_w(int tw) { return tw + 8; }
+__host__ __device__ constexpr int code_w(int tw) { return tw + 32; }
+__host__ __device__ constexpr int box_h(int tw) { return 1024 / tw + 2; }
+__host__ __device__ constexpr int box_bytes(int tw) { return box_w(tw) * box_h(tw) * 4; }
+__host__ __device__ constexpr int code_bytes(int tw) { return code_w(tw) * box_h(tw); }
+__host__ __device__ constexpr bool tile_ok(int tw) { return tw == 128 || tw == 64 || tw == 32; }
+constexpr int TWDEF = 128;           // tile width unless tuned otherwise
 constexpr long long TMA_WAIT_LIMIT = 1ll << 20;
 // polls before a ring-slot wait (full or empty) gives up; the drain of the
 // block's own copies at exit always uses TMA_WAIT_LIMIT
 __device__ long long g_slot_wait_limit = TMA_WAIT_LIMIT;
 
 constexpr int align128(int b) { return (b + 127) & ~127; }
-constexpr int BOX_BYTES = BOXW * BOXH * 4;    // 5440
-constexpr int OWN_BYTES = OWNW * ROWS * 4;    // 4096
-constexpr int CODE_BYTES = CODEW * BOXH;      // 1600
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// slot regions hold the largest box over the three tile widths
+constexpr int BOX_BYTES = cmax(box_bytes(128), cmax(box_bytes(64), box_bytes(32)));      // 5440
+constexpr int OWN_BYTES = 4096;                                                          // TW x TH floats
+constexpr int CODE_BYTES = cmax(code_bytes(128), cmax(code_bytes(64), code_bytes(32)));  // 2176
 
 template <int MODE>
 struct SlotLayout;
@@ -71,7 +88,7 @@ struct SlotLayout<0> {
     static constexpr int a = 0, b = align128(BOX_BYTES), x = -1, z = -1,
                          code = 2 * align128(BOX_BYTES);
     static constexpr int stride = align128(code + CODE_BYTES);
-    static constexpr unsigned tx = 2 * BOX_BYTES + CODE_BYTES;
+    __device__ static unsigned tx(int tw) { return 2 * box_bytes(tw) + code_bytes(tw); }
 };
 // update kernel: p box, x and z rows, codes
 template <>
@@ -79,14 +96,14 @@ struct SlotLayout<1> {
     static constexpr int a = 0, b = -1, x = align128(BOX_BYTES), z = x + OWN_BYTES,
                          code = z + OWN_BYTES;
     static constexpr int stride = align128(code + CODE_BYTES);
-    static constexpr unsigned tx = BOX_BYTES + 2 * OWN_BYTES + CODE_BYTES;
+    __device__ static unsigned tx(int tw) { return box_bytes(tw) + 2 * OWN_BYTES + code_bytes(tw); }
 };
 // apply: x box + codes
 template <>
 struct SlotLayout<2> {
     static constexpr int a = 0, b = -1, x = -1, z = -1, code = align128(BOX_BYTES);
     static constexpr int stride = align128(code + CODE_BYTES);
-    static constexpr unsigned tx = BOX_BYTES + CODE_BYTES;
+    __device__ static unsigned tx(int tw) { return box_bytes(tw) + code_bytes(tw); }
 };
 
 template <int MODE>
@@ -94,12 +111,12 @@ constexpr int smem_bytes() {
     return NSLOT * SlotLayout<MODE>::stride + 2 * NSLOT * 8;
 }
 
-struct Maps {
-    CUtensorMap a;      // streamed vector, 136 x 10 box (P: z, U: p, A: x)
-    CUtensorMap b;      // P: p_old, 136 x 10 box
-    CUtensorMap x;      // U: x, 128 x 8 box
-    CUtensorMap z;      // U: z, 128 x 8 box
-    CUtensorMap code;   // 160 x 10 box of code bytes
+struct Maps {  // boxes of the system's tile width TW (TH = 1024 / TW)
+    CUtensorMap a;      // streamed vector, (TW + 8) x (TH + 2) box (P: z, U: p, A: x)
+    CUtensorMap b;      // P: p_old, same box
+    CUtensorMap x;      // U: x, TW x TH box
+    CUtensorMap z;      // U: z, TW x TH box
+    CUtensorMap code;   // (TW + 32) x (TH + 2) box of code bytes
 };
 
 // One system of a launch table (device memory).
@@ -117,6 +134,7 @@ struct SysEntry {  // aligned as CUtensorMap
                         // [nitems + 2 li] and [nitems + 2 li + 1]
     unsigned int *cnt;  // items finished in the current launch
     int xtiles, ytiles, nchunk, KC, nitems, item_base;
+    int tw;             // tile width (128, 64 or 32) of the maps and items
 };
 
 // ------------------------------------------------------------------- PTX --
@@ -288,7 +306,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             for (;;) {
                 const int item = (int)atomicAdd(queue, 1u);
                 const bool end = item >= total_items;
-                int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1, cur = 0;
+                int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1, cur = 0, tw = TWDEF;
                 const SysEntry *e = tab;
                 if (!end) {
                     if constexpr (SINGLE) {
@@ -317,8 +335,9 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                     const int col = li / e->nchunk, c = li - col * e->nchunk;
                     kfirst = 1 + c * e->KC;
                     len = min(e->KC, e->pg.nz - 2 - c * e->KC);
-                    i0 = (col % e->xtiles) * OWNW;
-                    j0 = 1 + (col / e->xtiles) * ROWS;
+                    tw = e->tw;
+                    i0 = (col % e->xtiles) * tw;
+                    j0 = 1 + (col / e->xtiles) * tile_h(tw);
                 }
                 const Maps *m = MODE == MODE_P ? &e->P[cur] : (MODE == MODE_U ? &e->U[cur] : &e->A);
                 const int nplanes = end ? 1 : len + 2;
@@ -352,7 +371,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                     }
                     const uint32_t slot = smem_u32(smem + s * L::stride);
                     const int kp = kfirst - 1 + t;
-                    mbar_expect_tx(bar, L::tx);
+                    mbar_expect_tx(bar, L::tx(tw));
                     tma_load3(slot + L::a, &m->a, i0 - 4, j0 - 1, kp, bar);
                     if constexpr (MODE == MODE_P) tma_load3(slot + L::b, &m->b, i0 - 4, j0 - 1, kp, bar);
                     if constexpr (MODE == MODE_U) {
@@ -371,7 +390,19 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         }
     } else {
         // ------------------------------------------------------- consumers
-        const int r = w + 1;  // this row inside the halo boxes
+        // this lane's place in the tile, set per system from its tile width:
+        // box row r (tile row r - 1), x lane xl of the row (the row's lanes
+        // are 0 .. xlast), box and code row lengths bw and cw
+        int tw = TWDEF, bw = box_w(TWDEF), cw = code_w(TWDEF), xl = lane, xlast = 31, r = w + 1;
+        auto set_tile = [&](int t) {
+            const int sh = t == 128 ? 5 : (t == 64 ? 4 : 3);  // log2(lanes per row)
+            tw = t;
+            bw = box_w(t);
+            cw = code_w(t);
+            xl = lane & ((1 << sh) - 1);
+            xlast = (1 << sh) - 1;
+            r = 1 + w * (32 >> sh) + (lane >> sh);
+        };
         auto slot_ptr = [&](int t) { return smem + (t % NSLOT) * L::stride; };
         auto wait_full = [&](int t) -> bool {
             if (!mbar_wait(full0 + 8 * (t % NSLOT), (t / NSLOT) & 1, lim)) {
@@ -387,14 +418,14 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         float beta = 0.f;
         // streamed value (P: z + beta p_old) of box row rr
         auto val4 = [&](const uint8_t *sl, int rr, float (&v)[4]) {
-            const float *a = reinterpret_cast<const float *>(sl + L::a) + rr * BOXW + 4 + lane * 4;
+            const float *a = reinterpret_cast<const float *>(sl + L::a) + rr * bw + 4 + xl * 4;
             float4 t = *reinterpret_cast<const float4 *>(a);
             v[0] = t.x;
             v[1] = t.y;
             v[2] = t.z;
             v[3] = t.w;
             if (MODE == MODE_P) {
-                const float *b = reinterpret_cast<const float *>(sl + L::b) + rr * BOXW + 4 + lane * 4;
+                const float *b = reinterpret_cast<const float *>(sl + L::b) + rr * bw + 4 + xl * 4;
                 float4 u = *reinterpret_cast<const float4 *>(b);
                 v[0] += beta * u.x;
                 v[1] += beta * u.y;
@@ -403,12 +434,12 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             }
         };
         auto val1 = [&](const uint8_t *sl, int rr, int col) -> float {
-            float v = reinterpret_cast<const float *>(sl + L::a)[rr * BOXW + col];
-            if (MODE == MODE_P) v += beta * reinterpret_cast<const float *>(sl + L::b)[rr * BOXW + col];
+            float v = reinterpret_cast<const float *>(sl + L::a)[rr * bw + col];
+            if (MODE == MODE_P) v += beta * reinterpret_cast<const float *>(sl + L::b)[rr * bw + col];
             return v;
         };
         auto code4 = [&](const uint8_t *sl, int rr) -> uint32_t {
-            return *reinterpret_cast<const uint32_t *>(sl + L::code + rr * CODEW + 16 + lane * 4);
+            return *reinterpret_cast<const uint32_t *>(sl + L::code + rr * cw + 16 + xl * 4);
         };
 
         int gt = 0, nseg = 0;
@@ -433,6 +464,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             yg = e0.y;
             xg = e0.x;
             zg = e0.z;
+            set_tile(e0.tw);
             ksys = 0;
         }
         // Listed weights of this row at plane kp (codes in slot sl) go to L1
@@ -446,7 +478,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         auto prefetch_w = [&](const uint8_t *sl, int kp, int j, int ib, uint32_t cown,
                               uint32_t czb) {
             const uint32_t cyb = code4(sl, r - 1);
-            const uint32_t lc = lane == 0 ? (uint32_t)sl[L::code + r * CODEW + 15] : 0u;
+            const uint32_t lc = xl == 0 ? (uint32_t)sl[L::code + r * cw + 15] : 0u;
             const uint32_t need = (cown & 0x0E0E0E0Eu) | (cyb & 0x04040404u) |
                                   (czb & 0x08080808u) | (lc & 2u);
             if (!__any_sync(0xffffffffu, need != 0u)) return;
@@ -480,11 +512,12 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 yg = e->y;
                 xg = e->x;
                 zg = e->z;
+                set_tile(e->tw);
                 ksys = sys;
             }
             float *const outp = MODE == MODE_P ? (cur ? pb0 : pb1) : (MODE == MODE_A ? yg : nullptr);
-            const int j = j0 + w;
-            const int ib = i0 + lane * 4;
+            const int j = j0 + r - 1;
+            const int ib = i0 + xl * 4;
             const bool active = j <= g.ny - 2;
             const bool grp_ok = active && ib < g.sx;
             const int gt0 = gt;
@@ -516,7 +549,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 // path and issue the listed-weight gathers first, so that they
                 // are in flight while this warp waits for plane t+1
                 const uint32_t cym = code4(sc, r - 1);
-                const uint32_t lcode = sc[L::code + r * CODEW + 15 + lane * 4];
+                const uint32_t lcode = sc[L::code + r * cw + 15 + xl * 4];
                 const uint32_t cxl = (cc << 8) | lcode;
                 const uint32_t special = (cc & 0x0E0E0E0Eu) | (cxl & 0x02020202u) |
                                          (cym & 0x04040404u) | (cm & 0x08080808u);
@@ -547,19 +580,19 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                         wzm[q] = wz_valid ? wzc[q]
                                           : ((cz & 8) ? __ldg(cp.wz + pl + q - (int)g.sxy) : wp);
                     }
-                    if (lane == 0) wl = (lcode & 2) ? __ldg(cp.wx + pl - 1) : cp.pure((uint8_t)cc);
+                    if (xl == 0) wl = (lcode & 2) ? __ldg(cp.wx + pl - 1) : cp.pure((uint8_t)cc);
                 }
                 float ym[4], yp[4];
                 val4(sc, r - 1, ym);
                 val4(sc, r + 1, yp);
                 float left = __shfl_up_sync(0xffffffffu, pc[3], 1);
                 float right = __shfl_down_sync(0xffffffffu, pc[0], 1);
-                if (lane == 0) left = val1(sc, r, 3);
-                if (lane == 31) right = val1(sc, r, 4 + 32 * 4);
+                if (xl == 0) left = val1(sc, r, 3);
+                if (xl == xlast) right = val1(sc, r, 4 + tw);
                 float xv[4] = {0.f, 0.f, 0.f, 0.f}, zv[4] = {0.f, 0.f, 0.f, 0.f};
                 if (MODE == MODE_U) {
-                    float4 a = *reinterpret_cast<const float4 *>(sc + L::x + (w * OWNW + lane * 4) * 4);
-                    float4 b = *reinterpret_cast<const float4 *>(sc + L::z + (w * OWNW + lane * 4) * 4);
+                    float4 a = *reinterpret_cast<const float4 *>(sc + L::x + ((r - 1) * tw + xl * 4) * 4);
+                    float4 b = *reinterpret_cast<const float4 *>(sc + L::z + ((r - 1) * tw + xl * 4) * 4);
                     xv[0] = a.x;
                     xv[1] = a.y;
                     xv[2] = a.z;
@@ -582,7 +615,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                 if (!fast) {
                     // -x weight of point q is the +x weight of point q-1
                     const float wsh = __shfl_up_sync(0xffffffffu, wxp[3], 1);
-                    wxm[0] = lane == 0 ? wl : wsh;
+                    wxm[0] = xl == 0 ? wl : wsh;
                     wxm[1] = wxp[0];
                     wxm[2] = wxp[1];
                     wxm[3] = wxp[2];

@@ -66,3 +66,25 @@ def test_batch_of_one_and_errors(pb):
         pb.pb_solve_batch([s, s], pb.SolveOpts(precision=pb.MIXED))
     st = pb.pb_solve_batch([s], pb.SolveOpts(precision=pb.FP64, rtol=1e-8))
     assert st[0]["status"] == 0
+
+
+def test_batch_narrow_tiles_equal_alone(pb):
+    """Systems whose shapes run narrow tiles (32 x 32 and 64 x 16 points of a
+    plane) beside one on 128 x 8 tiles: each gives the same bits alone and in
+    the batch."""
+    shapes = [(43, 80, 211), (57, 150, 212), (71, 220, 213)]
+    opts = pb.SolveOpts(precision=pb.MIXED, rtol=1e-9)
+    alone = _systems(pb, shapes)
+    for s, tw in zip(alone, (32, 64, 128)):
+        pb.pb_set_tuning(s, pb.MIXED, 1, 6 + 10000 * tw)
+    ref = []
+    for s, tw in zip(alone, (32, 64, 128)):
+        st = pb.pb_solve(s, opts)
+        assert st["status"] == 0 and st["kc"] // 10000 == tw
+        ref.append((pb.pb_get_phi(s), st))
+    batch = _systems(pb, shapes[::-1])
+    stats = pb.pb_solve_batch(batch, opts)
+    for s, st, (phi, st_ref) in zip(batch, stats, ref[::-1]):
+        assert st["status"] == 0 and st["true_rel_res"] <= 1e-9
+        assert st["kc"] == st_ref["kc"] and st["iters_inner"] == st_ref["iters_inner"]
+        assert np.array_equal(pb.pb_get_phi(s), phi)

@@ -267,3 +267,36 @@ def test_too_many_balls_on_one_edge(pb):
     g = pb.pb_build_grid(spec, np.array([ball] * 48))
     assert g.info.n_cross > 0
     g.free()
+
+
+@pytest.mark.parametrize("tw", [32, 64, 128])
+def test_tile_widths(pb, case, tw, orc):
+    """The mixed-precision solve with each tile width of the TMA-staged PCG
+    kernels (tiles tw x 1024/tw points of a plane, fixed through
+    pb_set_tuning) meets the true residual and the energies of the oracle."""
+    s, og, ref = case["s"], case["og"], case["ref"]
+    pb.pb_coulomb_terms(s, pb.CT_SURFACE | pb.CT_PAIRS)
+    pb.pb_set_tuning(s, pb.MIXED, 1, 8 + 10000 * tw)
+    try:
+        st = pb.pb_solve(s, pb.SolveOpts(precision=pb.MIXED, rtol=1e-10))
+    finally:
+        pb.pb_set_tuning(s, pb.MIXED, 1, 8)
+    assert st["status"] == 0 and st["true_rel_res"] <= 1e-10
+    assert st["kc"] // 10000 == tw and st["kc"] % 1000 == 8
+    phi = pb.pb_get_phi(s)
+    x = phi - ref["phib"]
+    r = ref["f"] - orc.apply(og, ref["coef"], x)
+    interior = np.zeros(og.shape_zyx(), bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    interior = interior.reshape(-1)
+    assert np.linalg.norm(r[interior]) / np.linalg.norm(ref["f"][interior]) <= 1e-8
+    e = pb.pb_energy(s)
+    er = ref["energy"]
+    for k in ("e_pol", "e_ion_flux", "e_coul", "e_total", "e_ion_mc"):
+        assert abs(e[k] - er[k]) <= 1e-6 * max(abs(er[k]), 1e-3 * abs(er["e_pol"])), k
+
+
+def test_tile_width_rejected(pb, case):
+    from paper_2502_09323_gb300 import PBError
+    with pytest.raises(PBError, match="ARG"):
+        pb.pb_set_tuning(case["s"], pb.MIXED, 1, 8 + 10000 * 48)
