@@ -722,13 +722,17 @@ template <int MODE>
 pb_status tma_prepare() {
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<MODE, false>,
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<MODE, false, 0>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             tma::smem_bytes<MODE>());
+                                             tma::smem_bytes<MODE, 0>());
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_stencil_tma<MODE, true>,
+            e = cudaFuncSetAttribute(k_stencil_tma<MODE, true, 0>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     tma::smem_bytes<MODE>());
+                                     tma::smem_bytes<MODE, 0>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stencil_tma<MODE, true, tma::TWDEF>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tma::smem_bytes<MODE, tma::TWDEF>());
         if (e != cudaSuccess) {
             set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
             return PB_ERR_CUDA;
@@ -744,9 +748,9 @@ dim3 tma_grid(const PadGeo &g, int) {
     static int per_sm = 0;
     if (!per_sm) {
         if (tma_prepare<MODE_U>() != PB_OK ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<MODE_U, false>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<MODE_U, false, 0>,
                                                           tma::NTHREADS,
-                                                          tma::smem_bytes<MODE_U>()) != cudaSuccess ||
+                                                          tma::smem_bytes<MODE_U, 0>()) != cudaSuccess ||
             per_sm <= 0) {
             cudaGetLastError();
             per_sm = 2;
@@ -765,24 +769,34 @@ void tma_launch(const tma::SysEntry *dev_tab, int nsys, int total_items, unsigne
     // overlap: programmatic stream serialization, so that this launch's
     // blocks start (and set up) while the previous stencil kernel drains.
     static const tma::SysEntry zero{};
+    // one-system launches on the default tile width take the kernel that
+    // has it as a constant
+    const bool fixw = host_e0 && nsys == 1 && host_e0->tw == tma::TWDEF;
     if (host_e0 && nsys == 1 && overlap) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
         cfg.blockDim = dim3(tma::NTHREADS);
-        cfg.dynamicSmemBytes = tma::smem_bytes<MODE>();
+        cfg.dynamicSmemBytes = fixw ? tma::smem_bytes<MODE, tma::TWDEF>() : tma::smem_bytes<MODE, 0>();
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_stencil_tma<MODE, true>, dev_tab, nsys, total_items, queue,
-                           *host_e0);
-    } else if (host_e0 && nsys == 1)
-        k_stencil_tma<MODE, true><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(
+        if (fixw)
+            cudaLaunchKernelEx(&cfg, k_stencil_tma<MODE, true, tma::TWDEF>, dev_tab, nsys,
+                               total_items, queue, *host_e0);
+        else
+            cudaLaunchKernelEx(&cfg, k_stencil_tma<MODE, true, 0>, dev_tab, nsys, total_items,
+                               queue, *host_e0);
+    } else if (fixw)
+        k_stencil_tma<MODE, true, tma::TWDEF><<<grid, tma::NTHREADS, tma::smem_bytes<MODE, tma::TWDEF>(), s>>>(
+            dev_tab, nsys, total_items, queue, *host_e0);
+    else if (host_e0 && nsys == 1)
+        k_stencil_tma<MODE, true, 0><<<grid, tma::NTHREADS, tma::smem_bytes<MODE, 0>(), s>>>(
             dev_tab, nsys, total_items, queue, *host_e0);
     else
-        k_stencil_tma<MODE, false><<<grid, tma::NTHREADS, tma::smem_bytes<MODE>(), s>>>(
+        k_stencil_tma<MODE, false, 0><<<grid, tma::NTHREADS, tma::smem_bytes<MODE, 0>(), s>>>(
             dev_tab, nsys, total_items, queue, zero);
 }
 

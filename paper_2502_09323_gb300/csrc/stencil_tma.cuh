@@ -80,35 +80,40 @@ constexpr int BOX_BYTES = cmax(box_bytes(128), cmax(box_bytes(64), box_bytes(32)
 constexpr int OWN_BYTES = 4096;                                                          // TW x TH floats
 constexpr int CODE_BYTES = cmax(code_bytes(128), cmax(code_bytes(64), code_bytes(32)));  // 2176
 
-template <int MODE>
+// Slot regions hold the boxes of the tile width FIXW, or the largest over
+// the three widths (FIXW = 0).
+constexpr int box_region(int fixw) { return fixw ? box_bytes(fixw) : BOX_BYTES; }
+constexpr int code_region(int fixw) { return fixw ? code_bytes(fixw) : CODE_BYTES; }
+
+template <int MODE, int FIXW>
 struct SlotLayout;
 // direction kernel: z and p_old boxes + codes
-template <>
-struct SlotLayout<0> {
-    static constexpr int a = 0, b = align128(BOX_BYTES), x = -1, z = -1,
-                         code = 2 * align128(BOX_BYTES);
-    static constexpr int stride = align128(code + CODE_BYTES);
+template <int FIXW>
+struct SlotLayout<0, FIXW> {
+    static constexpr int a = 0, b = align128(box_region(FIXW)), x = -1, z = -1,
+                         code = 2 * align128(box_region(FIXW));
+    static constexpr int stride = align128(code + code_region(FIXW));
     __device__ static unsigned tx(int tw) { return 2 * box_bytes(tw) + code_bytes(tw); }
 };
 // update kernel: p box, x and z rows, codes
-template <>
-struct SlotLayout<1> {
-    static constexpr int a = 0, b = -1, x = align128(BOX_BYTES), z = x + OWN_BYTES,
+template <int FIXW>
+struct SlotLayout<1, FIXW> {
+    static constexpr int a = 0, b = -1, x = align128(box_region(FIXW)), z = x + OWN_BYTES,
                          code = z + OWN_BYTES;
-    static constexpr int stride = align128(code + CODE_BYTES);
+    static constexpr int stride = align128(code + code_region(FIXW));
     __device__ static unsigned tx(int tw) { return box_bytes(tw) + 2 * OWN_BYTES + code_bytes(tw); }
 };
 // apply: x box + codes
-template <>
-struct SlotLayout<2> {
-    static constexpr int a = 0, b = -1, x = -1, z = -1, code = align128(BOX_BYTES);
-    static constexpr int stride = align128(code + CODE_BYTES);
+template <int FIXW>
+struct SlotLayout<2, FIXW> {
+    static constexpr int a = 0, b = -1, x = -1, z = -1, code = align128(box_region(FIXW));
+    static constexpr int stride = align128(code + code_region(FIXW));
     __device__ static unsigned tx(int tw) { return box_bytes(tw) + code_bytes(tw); }
 };
 
-template <int MODE>
+template <int MODE, int FIXW>
 constexpr int smem_bytes() {
-    return NSLOT * SlotLayout<MODE>::stride + 2 * NSLOT * 8;
+    return NSLOT * SlotLayout<MODE, FIXW>::stride + 2 * NSLOT * 8;
 }
 
 struct Maps {  // boxes of the system's tile width TW (TH = 1024 / TW)
@@ -240,12 +245,14 @@ __device__ __forceinline__ void warp_nsum(float &s, float &c) {
 // geometry, coefficients) is the kernel parameter e0, so that its values are
 // read from the parameter bank instead of occupying registers; the
 // arithmetic is the same as in the table form.
-template <int MODE, bool SINGLE>
+// FIXW: the tile width as a constant (every system of the launch has it),
+// so that the lane and row indexing folds; 0 reads it per system.
+template <int MODE, bool SINGLE, int FIXW>
 __global__ void __launch_bounds__(tma::NTHREADS, 2)
 k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
               unsigned int *queue, const __grid_constant__ tma::SysEntry e0) {
     using namespace tma;
-    using L = SlotLayout<MODE>;
+    using L = SlotLayout<MODE, FIXW>;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort, s_nsys, s_total, s_skip;
     __shared__ int s_desc[NSLOT][7];  // i0, j0, kfirst, len, system, local item, parity
@@ -335,7 +342,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                     const int col = li / e->nchunk, c = li - col * e->nchunk;
                     kfirst = 1 + c * e->KC;
                     len = min(e->KC, e->pg.nz - 2 - c * e->KC);
-                    tw = e->tw;
+                    tw = FIXW ? FIXW : e->tw;
                     i0 = (col % e->xtiles) * tw;
                     j0 = 1 + (col / e->xtiles) * tile_h(tw);
                 }
@@ -393,9 +400,13 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
         // this lane's place in the tile, set per system from its tile width:
         // box row r (tile row r - 1), x lane xl of the row (the row's lanes
         // are 0 .. xlast), box and code row lengths bw and cw
-        int tw = TWDEF, bw = box_w(TWDEF), cw = code_w(TWDEF), xl = lane, xlast = 31, r = w + 1;
+        constexpr int TW0 = FIXW ? FIXW : TWDEF;
+        constexpr int SH0 = TW0 == 128 ? 5 : (TW0 == 64 ? 4 : 3);  // log2(lanes per row)
+        int tw = TW0, bw = box_w(TW0), cw = code_w(TW0), xl = lane & ((1 << SH0) - 1),
+            xlast = (1 << SH0) - 1, r = 1 + w * (32 >> SH0) + (lane >> SH0);
         auto set_tile = [&](int t) {
-            const int sh = t == 128 ? 5 : (t == 64 ? 4 : 3);  // log2(lanes per row)
+            if (FIXW) return;
+            const int sh = t == 128 ? 5 : (t == 64 ? 4 : 3);
             tw = t;
             bw = box_w(t);
             cw = code_w(t);
