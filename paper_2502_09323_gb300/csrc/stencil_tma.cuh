@@ -53,7 +53,7 @@ constexpr int NSLOT = 6;             // ring depth
 constexpr int NTHREADS = 32 * (ROWS + 1);
 // A tile is TW x (1024 / TW) points of one plane (TW = 128, 64 or 32, chosen
 // per grid shape): warp w owns tile rows w * RPW .. w * RPW + RPW - 1
-// (RPW = 32 / TW * 4 rows per warp), TW / 4 lanes per row, 4 points a lane.
+// (RPW = 128 / TW rows per warp), TW / 4 lanes per row, 4 points a lane.
 // Narrow tiles fit grids whose interior is not a multiple of 128 points
 // across (97- or 161-node grids leave a quarter or three eighths of a
 // 128-wide tile idle).  Boxes per plane:
