@@ -313,6 +313,13 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
             for (;;) {
                 const int item = (int)atomicAdd(queue, 1u);
                 const bool end = item >= total_items;
+                // The update kernel takes the items in reverse order: the
+                // direction kernel before it wrote p in item order, so the p
+                // of its last items is still in L2 when the update kernel
+                // starts there, and the next direction kernel starts on the
+                // z the update kernel wrote last.  Each item keeps its own
+                // partial slot, so the sums do not depend on the order.
+                const int it = MODE == MODE_U && !end ? total_items - 1 - item : item;
                 int sys = 0, li = 0, i0 = 0, j0 = 0, kfirst = 0, len = -1, cur = 0, tw = TWDEF;
                 const SysEntry *e = tab;
                 if (!end) {
@@ -320,10 +327,10 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                         sys = 0;
                         e = &e0;
                     } else {
-                        int lo = 0, hi = nsys - 1;  // last entry with item_base <= item
+                        int lo = 0, hi = nsys - 1;  // last entry with item_base <= it
                         while (lo < hi) {
                             const int mid = (lo + hi + 1) >> 1;
-                            if (tab[mid].item_base <= item) lo = mid;
+                            if (tab[mid].item_base <= it) lo = mid;
                             else hi = mid - 1;
                         }
                         sys = lo;
@@ -338,7 +345,7 @@ k_stencil_tma(const tma::SysEntry *__restrict__ tab, int nsys, int total_items,
                         if (cdone) continue;  // converged
                         cur = ccur;
                     }
-                    li = item - e->item_base;
+                    li = it - e->item_base;
                     const int col = li / e->nchunk, c = li - col * e->nchunk;
                     kfirst = 1 + c * e->KC;
                     len = min(e->KC, e->pg.nz - 2 - c * e->KC);
